@@ -51,6 +51,8 @@ def _load():
             lib.or_splitmix64.restype = u64
             lib.or_build.argtypes = [vp, vp, vp, u64, u32, u32, dbl, u32, dbl, dbl, ci, u64, ci]
             lib.or_build.restype = vp
+            lib.or_build_masked.argtypes = [vp, vp, vp, u64, u32, u32, dbl, u32, dbl, dbl, ci, u64, ci, vp]
+            lib.or_build_masked.restype = vp
             lib.or_free.argtypes = [vp]
             lib.or_list_sizes.argtypes = [vp, u32, vp]
             lib.or_list_get.argtypes = [vp, u32] + [vp] * 13
@@ -111,15 +113,21 @@ class Index:
     """Handle on an oracle index (Algorithm "Indexing with Seismic")."""
 
     def __init__(self, docs, lam, beta, alpha, quantize, seed, lambda_frac=0.0, beta_frac=0.0,
-                 threads=None):
+                 threads=None, terms=None):
+        """``terms``: build only these lists (enough for queries whose traversed
+        lists are among them); None builds every list."""
         lib = _load()
         self._keep = _csr_args(docs)
         self.docs = docs
         self.dim = docs.dim
         self.quantize = bool(quantize)
-        self._h = lib.or_build(_p(self._keep[0]), _p(self._keep[1]), _p(self._keep[2]), docs.n_rows,
-                               docs.dim, int(lam), float(lambda_frac), int(beta), float(beta_frac),
-                               float(alpha), int(bool(quantize)), int(seed), _threads(threads))
+        mask = None
+        if terms is not None:
+            mask = np.zeros(docs.dim, dtype=np.uint8)
+            mask[np.asarray(terms, dtype=np.int64)] = 1
+        self._h = lib.or_build_masked(_p(self._keep[0]), _p(self._keep[1]), _p(self._keep[2]), docs.n_rows,
+                                      docs.dim, int(lam), float(lambda_frac), int(beta), float(beta_frac),
+                                      float(alpha), int(bool(quantize)), int(seed), _threads(threads), _p(mask))
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
@@ -199,6 +207,18 @@ def pair_dots(docs, queries, qidx, didx):
     lib.or_pair_dots(_p(d_[0]), _p(d_[1]), _p(d_[2]), docs.n_rows, docs.dim, _p(q_[0]), _p(q_[1]),
                      _p(q_[2]), queries.n_rows, _p(qi), _p(di), len(qi), _p(out))
     return out
+
+
+def query_list_terms(queries, cut):
+    """The terms whose lists a cut-limited search traverses, per query (value desc, term asc)."""
+    out = set()
+    for i in range(queries.n_rows):
+        t, v = queries.row(i)
+        nz = v != 0
+        t, v = t[nz], v[nz]
+        o = np.lexsort((t, -v))[:cut]
+        out.update(int(x) for x in t[o])
+    return sorted(out)
 
 
 def recall_at_k(docs, queries, ids, exact_scores, k: int, rel_tol: float = 1e-6):

@@ -307,6 +307,7 @@ typedef struct {
   const csr_t *D;
   const inv_t *L;
   or_index *X;
+  const uint8_t *mask; /* NULL: every list; else build list t only where mask[t] */
   uint32_t lambda, beta;
   double lambda_frac, beta_frac, alpha;
   uint64_t seed;
@@ -345,6 +346,7 @@ static void build_list(void *vc, int64_t ti, int tid) {
   uint32_t t = (uint32_t)ti;
   olist_t *o = &c->X->lists[t];
   memset(o, 0, sizeof(*o));
+  if (c->mask && !c->mask[t]) return;
   uint64_t a = c->L->ptr[t], b = c->L->ptr[t + 1];
   uint32_t full = (uint32_t)(b - a);
   if (full == 0) return;
@@ -499,9 +501,12 @@ static void build_list(void *vc, int64_t ti, int tid) {
   free(ev);
 }
 
-or_index *or_build(const uint64_t *dip, const uint16_t *dt, const float *dv, uint64_t nd, uint32_t d,
-                   uint32_t lambda, double lambda_frac, uint32_t beta, double beta_frac, double alpha,
-                   int quantize, uint64_t seed, int threads) {
+/* Builds the index; with a non-NULL term_mask only the lists of the marked
+ * terms are built (the others stay empty), which is enough to run queries
+ * whose traversed lists are all marked. */
+or_index *or_build_masked(const uint64_t *dip, const uint16_t *dt, const float *dv, uint64_t nd, uint32_t d,
+                          uint32_t lambda, double lambda_frac, uint32_t beta, double beta_frac, double alpha,
+                          int quantize, uint64_t seed, int threads, const uint8_t *term_mask) {
   csr_t D = mk(dip, dt, dv, nd, d);
   inv_t L;
   transpose(&D, &L);
@@ -511,7 +516,7 @@ or_index *or_build(const uint64_t *dip, const uint16_t *dt, const float *dv, uin
   X->quantize = quantize;
   X->lists = (olist_t *)calloc(d, sizeof(olist_t));
   if (threads < 1) threads = 1;
-  bd_ctx c = {&D, &L, X, lambda, beta, lambda_frac, beta_frac, alpha, seed,
+  bd_ctx c = {&D, &L, X, term_mask, lambda, beta, lambda_frac, beta_frac, alpha, seed,
               NULL, NULL, NULL, NULL, NULL};
   c.dense = (double **)calloc(threads, sizeof(void *));
   c.mx = (float **)calloc(threads, sizeof(void *));
@@ -532,6 +537,13 @@ or_index *or_build(const uint64_t *dip, const uint16_t *dt, const float *dv, uin
   free(c.dense); free(c.mx); free(c.cnt); free(c.touched); free(c.mss);
   inv_free(&L);
   return X;
+}
+
+or_index *or_build(const uint64_t *dip, const uint16_t *dt, const float *dv, uint64_t nd, uint32_t d,
+                   uint32_t lambda, double lambda_frac, uint32_t beta, double beta_frac, double alpha,
+                   int quantize, uint64_t seed, int threads) {
+  return or_build_masked(dip, dt, dv, nd, d, lambda, lambda_frac, beta, beta_frac, alpha, quantize, seed,
+                         threads, NULL);
 }
 
 void or_free(or_index *X) {

@@ -1,0 +1,698 @@
+// Index construction: Algorithm "Indexing with Seismic" (Section 4.4).
+//
+// Host (threads): validation, forward-index layout, posting lists pruned to
+// their top-lambda values (Set alpha-MSS, fixed-lambda form of Table 4, or the
+// proportional form of Definition "Set alpha-MSS"), centroid sampling,
+// blocks, max summaries (Eq. "summary") with their alpha-MSS and 8-bit
+// quantisation (Section 4.1.3), and the term-major summary layout.
+// Device: the shallow k-means assignment (Section 4.1.2), which dominates the
+// build: every list member against every centroid of its list.
+#include <algorithm>
+#include <cmath>
+#include <memory>
+
+#include "seismic_impl.h"
+
+namespace seismic {
+
+namespace {
+
+struct HostCsr {
+  std::vector<uint64_t> ip;
+  std::vector<uint16_t> t;
+  std::vector<float> v;
+  uint64_t n = 0;
+  uint32_t d = 0;
+};
+
+// Copies `m` to host (if needed), validates it and drops explicit zeros.
+int fetch_docs(const seismic_csr *m, HostCsr &h) {
+  if (!m || !m->indptr || m->n_rows == 0) return fail(SEISMIC_EINVAL, "documents: empty or NULL CSR");
+  if (m->dim == 0 || m->dim > 65535) return fail(SEISMIC_EINVAL, "documents: dim must be in 1..65535");
+  if (m->n_rows >= 0xFFFFFFFFull) return fail(SEISMIC_EINVAL, "documents: more than 2^32-2 rows");
+  std::vector<uint64_t> ip(m->n_rows + 1);
+  const uint64_t *ipp = m->indptr;
+  const uint16_t *tp = m->terms;
+  const float *vp = m->vals;
+  std::vector<uint16_t> tbuf;
+  std::vector<float> vbuf;
+  if (m->on_device) {
+    SZ_CUDA(cudaMemcpy(ip.data(), m->indptr, ip.size() * 8, cudaMemcpyDeviceToHost));
+    uint64_t nnz = ip.back();
+    tbuf.resize(nnz);
+    vbuf.resize(nnz);
+    if (nnz) {
+      SZ_CUDA(cudaMemcpy(tbuf.data(), m->terms, nnz * 2, cudaMemcpyDeviceToHost));
+      SZ_CUDA(cudaMemcpy(vbuf.data(), m->vals, nnz * 4, cudaMemcpyDeviceToHost));
+    }
+    ipp = ip.data();
+    tp = tbuf.data();
+    vp = vbuf.data();
+  }
+  seismic_csr hc = *m;
+  hc.indptr = ipp;
+  hc.terms = tp;
+  hc.vals = vp;
+  hc.on_device = 0;
+  int rc = validate_host_csr(&hc, "documents", m->dim);
+  if (rc) return rc;
+  h.n = m->n_rows;
+  h.d = m->dim;
+  h.ip.assign(h.n + 1, 0);
+  uint64_t nnz = 0;
+  for (uint64_t i = 0; i < h.n; i++) {
+    uint64_t c = 0;
+    for (uint64_t p = ipp[i]; p < ipp[i + 1]; p++) c += vp[p] != 0.0f;
+    if (c > kMaxRowNnzBuild)
+      return fail(SEISMIC_EINVAL, "documents: a row has more than " + std::to_string(kMaxRowNnzBuild) +
+                                      " nonzeros");
+    nnz += c;
+    h.ip[i + 1] = nnz;
+  }
+  h.t.resize(nnz);
+  h.v.resize(nnz);
+  for (uint64_t i = 0, o = 0; i < h.n; i++)
+    for (uint64_t p = ipp[i]; p < ipp[i + 1]; p++)
+      if (vp[p] != 0.0f) {
+        h.t[o] = tp[p];
+        h.v[o] = vp[p];
+        o++;
+      }
+  return SEISMIC_OK;
+}
+
+uint64_t splitmix64_next(uint64_t &state) {
+  uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// ------------------------------------------------------------------ clustering kernel
+// One CTA per list.  Centroids are taken in chunks whose nonzeros fit in
+// shared memory; a chunk is turned into a small inverted index (term ->
+// (centroid, value)) addressed through a bitmap + popcount rank over the
+// vocabulary.  Each thread then scores one list member against the whole
+// chunk: it walks the member's terms in ascending order and, for each term the
+// chunk holds, adds the exact fp64 product into its per-centroid fp64
+// accumulators.  Each accumulator thus receives the nonzero products of the
+// two vectors' common terms in ascending term order: the same fp64 sum as a
+// sequential merge of the two sorted rows.  Argmax ties keep the lower
+// centroid index.
+constexpr int kAsgThreads = 128;
+constexpr int kAsgCC = 64;        // centroids per chunk (cluster index fits in u8)
+constexpr int kAsgMaxEnt = 8192;  // nonzeros per chunk (= kMaxRowNnzBuild bound below)
+static_assert(kMaxRowNnzBuild <= kAsgMaxEnt, "a centroid row must fit one chunk");
+
+__device__ __forceinline__ void asg_scan_rank(const uint32_t *bits, uint16_t *rank, uint32_t W, uint32_t *wtmp) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kAsgThreads / 32;
+  uint32_t per = (W + kAsgThreads - 1) / kAsgThreads, lo = min(W, tid * per), hi = min(W, lo + per);
+  uint32_t s = 0;
+  for (uint32_t i = lo; i < hi; i++) s += __popc(bits[i]);
+  uint32_t x = s;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wtmp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t v = lane < nw ? wtmp[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
+    }
+    if (lane < nw) wtmp[lane] = v;
+  }
+  __syncthreads();
+  uint32_t base = (warp ? wtmp[warp - 1] : 0) + x - s;
+  for (uint32_t i = lo; i < hi; i++) {
+    rank[i] = (uint16_t)base;
+    base += __popc(bits[i]);
+  }
+  __syncthreads();
+}
+
+// exclusive scan of cnt[0..n) into off[0..n] (u16) and cnt (cursor copy)
+__device__ __forceinline__ void asg_scan_counts(uint32_t *cnt, uint16_t *off, uint32_t n, uint32_t *wtmp) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kAsgThreads / 32;
+  uint32_t per = (n + kAsgThreads - 1) / kAsgThreads, lo = min(n, tid * per), hi = min(n, lo + per);
+  uint32_t s = 0;
+  for (uint32_t i = lo; i < hi; i++) s += cnt[i];
+  uint32_t x = s;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wtmp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t v = lane < nw ? wtmp[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
+    }
+    if (lane < nw) wtmp[lane] = v;
+  }
+  __syncthreads();
+  uint32_t base = (warp ? wtmp[warp - 1] : 0) + x - s;
+  for (uint32_t i = lo; i < hi; i++) {
+    uint32_t c = cnt[i];
+    off[i] = (uint16_t)base;
+    cnt[i] = base;
+    base += c;
+  }
+  if (tid == kAsgThreads - 1) off[n] = (uint16_t)wtmp[nw - 1];
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kAsgThreads) k_assign(
+    const uint32_t *__restrict__ work, uint32_t n_work, const uint32_t *__restrict__ list_ptr,
+    const uint32_t *__restrict__ list_doc, const uint32_t *__restrict__ cent_ptr,
+    const uint32_t *__restrict__ cent_doc, const uint64_t *__restrict__ indptr,
+    const uint16_t *__restrict__ terms, const float *__restrict__ vals, uint32_t dim,
+    double *__restrict__ best, uint32_t *__restrict__ assign) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const uint32_t W = (dim + 31) / 32;
+  double *acc = reinterpret_cast<double *>(smem);                    // kAsgCC * kAsgThreads
+  float *ent_w = reinterpret_cast<float *>(acc + kAsgCC * kAsgThreads);  // kAsgMaxEnt
+  uint32_t *ccur = reinterpret_cast<uint32_t *>(ent_w + kAsgMaxEnt);     // kAsgMaxEnt + 1
+  uint32_t *cbits = ccur + (kAsgMaxEnt + 1);                              // W
+  uint16_t *coff = reinterpret_cast<uint16_t *>(cbits + W);               // kAsgMaxEnt + 1
+  uint16_t *crank = coff + (kAsgMaxEnt + 1);                              // W
+  uint8_t *ent_c = reinterpret_cast<uint8_t *>(crank + W);                // kAsgMaxEnt
+  __shared__ uint32_t wtmp[32];
+  const int tid = threadIdx.x;
+
+  for (uint32_t wi = blockIdx.x; wi < n_work; wi += gridDim.x) {
+    const uint32_t t = work[wi];
+    const uint32_t lp0 = list_ptr[t], n = list_ptr[t + 1] - lp0;
+    const uint32_t cp0 = cent_ptr[t], nb = cent_ptr[t + 1] - cp0;
+    uint32_t c0 = 0;
+    while (c0 < nb) {
+      uint32_t c1 = c0, ent = 0;
+      while (c1 < nb && c1 - c0 < (uint32_t)kAsgCC) {
+        uint32_t cd = cent_doc[cp0 + c1];
+        uint32_t len = (uint32_t)(indptr[cd + 1] - indptr[cd]);
+        if (c1 > c0 && ent + len > (uint32_t)kAsgMaxEnt) break;
+        ent += len;
+        c1++;
+      }
+      for (uint32_t i = tid; i < W; i += kAsgThreads) cbits[i] = 0;
+      __syncthreads();
+      for (uint32_t c = c0; c < c1; c++) {
+        uint32_t cd = cent_doc[cp0 + c];
+        for (uint64_t p = indptr[cd] + tid; p < indptr[cd + 1]; p += kAsgThreads) {
+          uint16_t s = terms[p];
+          atomicOr(&cbits[s >> 5], 1u << (s & 31));
+        }
+      }
+      __syncthreads();
+      asg_scan_rank(cbits, crank, W, wtmp);
+      const uint32_t ndist = (W ? crank[W - 1] + __popc(cbits[W - 1]) : 0);
+      for (uint32_t i = tid; i <= ndist; i += kAsgThreads) ccur[i] = 0;
+      __syncthreads();
+      for (uint32_t c = c0; c < c1; c++) {
+        uint32_t cd = cent_doc[cp0 + c];
+        for (uint64_t p = indptr[cd] + tid; p < indptr[cd + 1]; p += kAsgThreads) {
+          uint16_t s = terms[p];
+          uint32_t w = cbits[s >> 5];
+          uint32_t idx = crank[s >> 5] + __popc(w & ((1u << (s & 31)) - 1u));
+          atomicAdd(&ccur[idx], 1u);
+        }
+      }
+      __syncthreads();
+      asg_scan_counts(ccur, coff, ndist, wtmp);
+      for (uint32_t c = c0; c < c1; c++) {
+        uint32_t cd = cent_doc[cp0 + c];
+        for (uint64_t p = indptr[cd] + tid; p < indptr[cd + 1]; p += kAsgThreads) {
+          uint16_t s = terms[p];
+          uint32_t w = cbits[s >> 5];
+          uint32_t idx = crank[s >> 5] + __popc(w & ((1u << (s & 31)) - 1u));
+          uint32_t pos = atomicAdd(&ccur[idx], 1u);
+          ent_c[pos] = (uint8_t)(c - c0);
+          ent_w[pos] = vals[p];
+        }
+      }
+      __syncthreads();
+      const uint32_t ncc = c1 - c0;
+      double *a = acc + tid;
+      for (uint32_t i = tid; i < n; i += kAsgThreads) {
+        const uint32_t j = list_doc[lp0 + i];
+        for (uint32_t cc = 0; cc < ncc; cc++) a[cc * kAsgThreads] = 0.0;
+        for (uint64_t p = indptr[j]; p < indptr[j + 1]; p++) {
+          const uint16_t s = terms[p];
+          const uint32_t w = cbits[s >> 5];
+          const uint32_t bit = 1u << (s & 31);
+          if (!(w & bit)) continue;
+          const uint32_t idx = crank[s >> 5] + __popc(w & (bit - 1u));
+          const double u = (double)vals[p];
+          for (uint32_t e = coff[idx]; e < coff[idx + 1]; e++)
+            a[(uint32_t)ent_c[e] * kAsgThreads] = __dadd_rn(a[(uint32_t)ent_c[e] * kAsgThreads],
+                                                              __dmul_rn(u, (double)ent_w[e]));
+        }
+        double bv;
+        uint32_t bc, cc0;
+        if (c0 == 0) {
+          bv = a[0];
+          bc = 0;
+          cc0 = 1;
+        } else {
+          bv = best[lp0 + i];
+          bc = assign[lp0 + i];
+          cc0 = 0;
+        }
+        for (uint32_t cc = cc0; cc < ncc; cc++) {
+          double v = a[cc * kAsgThreads];
+          if (v > bv) {
+            bv = v;
+            bc = c0 + cc;
+          }
+        }
+        best[lp0 + i] = bv;
+        assign[lp0 + i] = bc;
+      }
+      __syncthreads();
+      c0 = c1;
+    }
+  }
+}
+
+size_t asg_smem_bytes(uint32_t dim) {
+  uint32_t W = (dim + 31) / 32;
+  return (size_t)kAsgCC * kAsgThreads * 8 + (size_t)kAsgMaxEnt * 4 + (size_t)(kAsgMaxEnt + 1) * 4 + W * 4 +
+         (size_t)(kAsgMaxEnt + 1) * 2 + W * 2 + kAsgMaxEnt + 16;
+}
+
+struct Mss {
+  float a;
+  uint16_t t;
+  uint32_t i;
+};
+
+}  // namespace
+
+int validate_host_csr(const seismic_csr *m, const char *what, uint32_t dim_expect) {
+  std::string w(what);
+  if (!m || !m->indptr) return fail(SEISMIC_EINVAL, w + ": NULL CSR");
+  if (m->dim != dim_expect) return fail(SEISMIC_EINVAL, w + ": dim differs from the index");
+  if (m->indptr[0] != 0) return fail(SEISMIC_EINVAL, w + ": indptr[0] != 0");
+  uint64_t nnz = m->indptr[m->n_rows];
+  if (nnz && (!m->terms || !m->vals)) return fail(SEISMIC_EINVAL, w + ": NULL terms/vals");
+  for (uint64_t i = 0; i < m->n_rows; i++) {
+    if (m->indptr[i + 1] < m->indptr[i]) return fail(SEISMIC_EINVAL, w + ": indptr decreases at row " + std::to_string(i));
+    for (uint64_t p = m->indptr[i]; p < m->indptr[i + 1]; p++) {
+      if (m->terms[p] >= m->dim) return fail(SEISMIC_EINVAL, w + ": term id >= dim in row " + std::to_string(i));
+      if (p > m->indptr[i] && m->terms[p] <= m->terms[p - 1])
+        return fail(SEISMIC_EINVAL, w + ": terms not strictly increasing in row " + std::to_string(i));
+      if (!std::isfinite(m->vals[p])) return fail(SEISMIC_EINVAL, w + ": non-finite value in row " + std::to_string(i));
+    }
+  }
+  return SEISMIC_OK;
+}
+
+uint64_t device_bytes(const seismic_index *ix) {
+  const DevBuf *b[] = {&ix->fwd_cptr, &ix->fwd_data, &ix->fwd_nnz, &ix->list_ptr, &ix->list_doc, &ix->cent,
+                       &ix->blk_ptr, &ix->bdoc_ptr, &ix->bdoc, &ix->blk_m, &ix->blk_size, &ix->sum_ptr,
+                       &ix->sum_term, &ix->sum_val, &ix->sum_code, &ix->sdir, &ix->scol_blk, &ix->scol_code,
+                       &ix->scol_val, &ix->full_ptr, &ix->full_doc, &ix->full_val, &ix->knn, &ix->mlp};
+  uint64_t s = 0;
+  for (auto *x : b) s += x->bytes;
+  return s;
+}
+
+int build_index(const seismic_csr *docs, const seismic_build_params *bp, seismic_index **out) {
+  if (!bp || !out) return fail(SEISMIC_EINVAL, "NULL params/out");
+  if (!(bp->alpha > 0.0 && bp->alpha <= 1.0)) return fail(SEISMIC_EINVAL, "alpha must be in (0, 1]");
+  if (bp->beta == 0 && !(bp->beta_frac > 0.0)) return fail(SEISMIC_EINVAL, "beta must be >= 1");
+  if (bp->lambda_frac < 0.0 || bp->lambda_frac > 1.0 || bp->beta_frac < 0.0 || bp->beta_frac > 1.0)
+    return fail(SEISMIC_EINVAL, "lambda_frac / beta_frac must be in [0, 1]");
+  HostCsr D;
+  int rc = fetch_docs(docs, D);
+  if (rc) return rc;
+  const int T = hw_threads(bp->threads);
+  const uint32_t d = D.d;
+  std::unique_ptr<seismic_index> ix(new seismic_index());
+  SZ_CUDA(cudaGetDevice(&ix->device));
+  ix->dim = d;
+  ix->n_docs = D.n;
+  ix->nnz = D.ip.back();
+  ix->bp = *bp;
+
+  // ---- forward index, padded 8-entry chunks
+  {
+    std::vector<uint32_t> cptr(D.n + 1, 0);
+    std::vector<uint16_t> rnnz(D.n);
+    for (uint64_t i = 0; i < D.n; i++) {
+      uint64_t n = D.ip[i + 1] - D.ip[i];
+      rnnz[i] = (uint16_t)n;
+      uint64_t c = cptr[i] + (n + kChunk - 1) / kChunk;
+      if (c > 0xFFFFFFFFull) return fail(SEISMIC_EINVAL, "forward index exceeds 2^32 chunks");
+      cptr[i + 1] = (uint32_t)c;
+    }
+    std::vector<uint8_t> data((size_t)cptr[D.n] * kChunkBytes, 0);
+    parallel_for((int64_t)D.n, T, [&](int64_t i, int) {
+      uint64_t n = D.ip[i + 1] - D.ip[i];
+      uint32_t P = (cptr[i + 1] - cptr[i]) * kChunk;
+      uint8_t *rec = data.data() + (size_t)cptr[i] * kChunkBytes;
+      uint16_t *tt = reinterpret_cast<uint16_t *>(rec);
+      float *vv = reinterpret_cast<float *>(rec + 2 * (size_t)P);
+      for (uint64_t p = 0; p < n; p++) {
+        tt[p] = D.t[D.ip[i] + p];
+        vv[p] = D.v[D.ip[i] + p];
+      }
+    });
+    if ((rc = upload(ix->fwd_cptr, cptr)) || (rc = upload(ix->fwd_data, data)) || (rc = upload(ix->fwd_nnz, rnnz)))
+      return rc;
+  }
+
+  // ---- full inverted lists (ascending doc ids)
+  std::vector<uint64_t> fptr(d + 1, 0);
+  std::vector<uint32_t> fdoc(ix->nnz);
+  std::vector<float> fval(ix->nnz);
+  {
+    for (uint64_t p = 0; p < ix->nnz; p++) fptr[D.t[p] + 1]++;
+    for (uint32_t t = 0; t < d; t++) fptr[t + 1] += fptr[t];
+    std::vector<uint64_t> cur(fptr.begin(), fptr.end() - 1);
+    for (uint64_t i = 0; i < D.n; i++)
+      for (uint64_t p = D.ip[i]; p < D.ip[i + 1]; p++) {
+        uint64_t o = cur[D.t[p]]++;
+        fdoc[o] = (uint32_t)i;
+        fval[o] = D.v[p];
+      }
+  }
+  if (bp->keep_full_lists) {
+    if (ix->nnz > 0xFFFFFFFFull) return fail(SEISMIC_EINVAL, "keep_full_lists: more than 2^32 nonzeros");
+    std::vector<uint32_t> fp32(fptr.begin(), fptr.end());
+    if ((rc = upload(ix->full_ptr, fp32)) || (rc = upload(ix->full_doc, fdoc)) || (rc = upload(ix->full_val, fval)))
+      return rc;
+    ix->has_full = 1;
+  }
+
+  // ---- pruned lists: top-lambda_t postings by (value desc, doc asc)
+  std::vector<uint32_t> lptr(d + 1, 0);
+  for (uint32_t t = 0; t < d; t++) {
+    uint64_t full = fptr[t + 1] - fptr[t];
+    uint64_t lam;
+    if (bp->lambda_frac > 0.0) lam = (uint64_t)std::ceil(bp->lambda_frac * (double)full);
+    else lam = bp->lambda ? bp->lambda : full;
+    if (lam > full) lam = full;
+    if ((uint64_t)lptr[t] + lam > 0xFFFFFFFFull) return fail(SEISMIC_EINVAL, "more than 2^32 postings");
+    lptr[t + 1] = lptr[t] + (uint32_t)lam;
+  }
+  const uint64_t npost = lptr[d];
+  ix->n_postings = npost;
+  std::vector<uint32_t> ldoc(npost);
+  std::vector<float> lval(npost);
+  parallel_for(d, T, [&](int64_t t, int) {
+    uint64_t a = fptr[t], n = fptr[t + 1] - a;
+    if (!n) return;
+    std::vector<uint32_t> idx(n);
+    for (uint64_t i = 0; i < n; i++) idx[i] = (uint32_t)i;
+    uint64_t lam = lptr[t + 1] - lptr[t];
+    auto cmp = [&](uint32_t x, uint32_t y) {
+      float vx = fval[a + x], vy = fval[a + y];
+      if (vx != vy) return vx > vy;
+      return fdoc[a + x] < fdoc[a + y];
+    };
+    if (lam < n) std::partial_sort(idx.begin(), idx.begin() + lam, idx.end(), cmp);
+    else std::sort(idx.begin(), idx.end(), cmp);
+    for (uint64_t i = 0; i < lam; i++) {
+      ldoc[lptr[t] + i] = fdoc[a + idx[i]];
+      lval[lptr[t] + i] = fval[a + idx[i]];
+    }
+  });
+  std::vector<uint64_t>().swap(fptr);
+  std::vector<uint32_t>().swap(fdoc);
+  std::vector<float>().swap(fval);
+
+  // ---- centroids: partial Fisher-Yates per list, splitmix64(seed ^ t*golden)
+  std::vector<uint32_t> cptr2(d + 1, 0);
+  for (uint32_t t = 0; t < d; t++) {
+    uint32_t n = lptr[t + 1] - lptr[t];
+    uint32_t nb = 0;
+    if (n) {
+      nb = bp->beta_frac > 0.0 ? (uint32_t)std::ceil(bp->beta_frac * (double)n) : bp->beta;
+      nb = std::max(1u, std::min(nb, n));
+    }
+    cptr2[t + 1] = cptr2[t] + nb;
+  }
+  std::vector<uint32_t> cdoc(cptr2[d]);
+  parallel_for(d, T, [&](int64_t t, int) {
+    uint32_t n = lptr[t + 1] - lptr[t], nb = cptr2[t + 1] - cptr2[t];
+    if (!nb) return;
+    std::vector<uint32_t> pos(n);
+    for (uint32_t i = 0; i < n; i++) pos[i] = i;
+    uint64_t st = bp->seed ^ ((uint64_t)t * 0x9E3779B97F4A7C15ull);
+    for (uint32_t i = 0; i < nb; i++) {
+      uint32_t j = i + (uint32_t)(splitmix64_next(st) % (uint64_t)(n - i));
+      std::swap(pos[i], pos[j]);
+      cdoc[cptr2[t] + i] = ldoc[lptr[t] + pos[i]];
+    }
+  });
+
+  // ---- clustering on the device
+  std::vector<uint32_t> assign(npost);
+  {
+    std::vector<uint32_t> work;
+    for (uint32_t t = 0; t < d; t++)
+      if (lptr[t + 1] > lptr[t]) work.push_back(t);
+    DevBuf d_work, d_lptr, d_ldoc, d_cptr, d_cdoc, d_ip, d_t, d_v, d_best, d_asg;
+    if ((rc = upload(d_work, work)) || (rc = upload(d_lptr, lptr)) || (rc = upload(d_ldoc, ldoc)) ||
+        (rc = upload(d_cptr, cptr2)) || (rc = upload(d_cdoc, cdoc)) || (rc = upload(d_ip, D.ip)) ||
+        (rc = upload(d_t, D.t)) || (rc = upload(d_v, D.v)) || (rc = d_best.alloc(npost * 8)) ||
+        (rc = d_asg.alloc(npost * 4)))
+      return rc;
+    size_t smem = asg_smem_bytes(d);
+    SZ_CUDA(cudaFuncSetAttribute(k_assign, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int sms = 1;
+    SZ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device));
+    uint32_t grid = (uint32_t)std::min<size_t>(work.size(), (size_t)sms * 8);
+    if (grid) {
+      k_assign<<<grid, kAsgThreads, smem>>>(d_work.as<uint32_t>(), (uint32_t)work.size(), d_lptr.as<uint32_t>(),
+                                            d_ldoc.as<uint32_t>(), d_cptr.as<uint32_t>(), d_cdoc.as<uint32_t>(),
+                                            d_ip.as<uint64_t>(), d_t.as<uint16_t>(), d_v.as<float>(), d,
+                                            d_best.as<double>(), d_asg.as<uint32_t>());
+      SZ_CUDA(cudaGetLastError());
+      SZ_CUDA(cudaDeviceSynchronize());
+    }
+    if (npost) SZ_CUDA(cudaMemcpy(assign.data(), d_asg.p, npost * 4, cudaMemcpyDeviceToHost));
+  }
+
+  // ---- blocks (non-empty clusters in centroid order; members ascending)
+  std::vector<uint32_t> nblk_of(d, 0);
+  parallel_for(d, T, [&](int64_t t, int) {
+    uint32_t nb = cptr2[t + 1] - cptr2[t];
+    if (!nb) return;
+    std::vector<uint8_t> used(nb, 0);
+    for (uint32_t p = lptr[t]; p < lptr[t + 1]; p++) used[assign[p]] = 1;
+    uint32_t c = 0;
+    for (uint8_t u : used) c += u;
+    nblk_of[t] = c;
+  });
+  std::vector<uint32_t> bptr(d + 1, 0);
+  for (uint32_t t = 0; t < d; t++) bptr[t + 1] = bptr[t] + nblk_of[t];
+  const uint32_t nblk = bptr[d];
+  ix->n_blocks = nblk;
+  std::vector<uint32_t> bdptr(nblk + 1, 0), bdoc(npost);
+  parallel_for(d, T, [&](int64_t t, int) {
+    uint32_t nb = cptr2[t + 1] - cptr2[t];
+    if (!nb) return;
+    std::vector<uint32_t> cnt(nb, 0), start(nb, 0);
+    for (uint32_t p = lptr[t]; p < lptr[t + 1]; p++) cnt[assign[p]]++;
+    uint32_t g = bptr[t], off = lptr[t];  // members of list t occupy [lptr[t], lptr[t+1])
+    for (uint32_t c = 0; c < nb; c++) {
+      if (!cnt[c]) continue;
+      bdptr[g] = off;  // written per block; the last entry is set below
+      start[c] = off;
+      off += cnt[c];
+      g++;
+    }
+    for (uint32_t p = lptr[t]; p < lptr[t + 1]; p++) bdoc[start[assign[p]]++] = ldoc[p];
+    g = bptr[t];
+    for (uint32_t c = 0; c < nb; c++) {
+      if (!cnt[c]) continue;
+      std::sort(bdoc.begin() + bdptr[g], bdoc.begin() + bdptr[g] + cnt[c]);
+      g++;
+    }
+  });
+  bdptr[nblk] = (uint32_t)npost;
+  uint32_t maxbd = 0, maxnb = 0;
+  for (uint32_t g = 0; g < nblk; g++) maxbd = std::max(maxbd, bdptr[g + 1] - bdptr[g]);
+  for (uint32_t t = 0; t < d; t++) maxnb = std::max(maxnb, nblk_of[t]);
+  ix->max_block_docs = maxbd;
+  ix->max_blocks_per_list = maxnb;
+  std::vector<uint32_t>().swap(cdoc);
+
+  // ---- summaries: max vector, alpha-MSS, quantisation (per list, block-major)
+  struct ListSum {
+    std::vector<uint32_t> cnt;  // kept entries per block
+    std::vector<uint16_t> term;
+    std::vector<float> val;
+    std::vector<uint8_t> code;
+    std::vector<float> m, size;
+  };
+  std::vector<ListSum> ls(d);
+  const double alpha = bp->alpha;
+  const int quant = bp->quantize_u8 ? 1 : 0;
+  {
+    std::vector<std::vector<float>> mx(T, std::vector<float>(d));
+    std::vector<std::vector<uint32_t>> cn(T, std::vector<uint32_t>(d, 0));
+    std::vector<std::vector<uint16_t>> touched(T, std::vector<uint16_t>(d));
+    std::vector<std::vector<Mss>> ms(T, std::vector<Mss>(d));
+    parallel_for(d, T, [&](int64_t t, int tid) {
+      ListSum &L = ls[t];
+      uint32_t g0 = bptr[t], g1 = bptr[t + 1];
+      L.cnt.resize(g1 - g0);
+      L.m.resize(g1 - g0);
+      L.size.resize(g1 - g0);
+      float *mxx = mx[tid].data();
+      uint32_t *cc = cn[tid].data();
+      uint16_t *tch = touched[tid].data();
+      Mss *buf = ms[tid].data();
+      for (uint32_t g = g0; g < g1; g++) {
+        uint32_t bs = bdptr[g + 1] - bdptr[g], nt = 0;
+        for (uint32_t m = bdptr[g]; m < bdptr[g + 1]; m++) {
+          uint32_t j = bdoc[m];
+          for (uint64_t p = D.ip[j]; p < D.ip[j + 1]; p++) {
+            uint16_t s = D.t[p];
+            float v = D.v[p];
+            if (cc[s] == 0) {
+              tch[nt++] = s;
+              mxx[s] = v;
+            } else if (v > mxx[s]) {
+              mxx[s] = v;
+            }
+            cc[s]++;
+          }
+        }
+        uint32_t ne = 0;
+        for (uint32_t i = 0; i < nt; i++) {
+          uint16_t s = tch[i];
+          float phi = mxx[s];
+          if (cc[s] < bs && phi < 0.0f) phi = 0.0f;  // members without the term contribute 0
+          cc[s] = 0;
+          if (phi != 0.0f) {
+            buf[ne].a = std::fabs(phi);
+            buf[ne].t = s;
+            buf[ne].i = *reinterpret_cast<uint32_t *>(&phi);
+            ne++;
+          }
+        }
+        std::sort(buf, buf + ne, [](const Mss &x, const Mss &y) {
+          if (x.a != y.a) return x.a > y.a;
+          return x.t < y.t;
+        });
+        double total = 0.0;
+        for (uint32_t i = 0; i < ne; i++) total += (double)buf[i].a;
+        double target = alpha * total, c = 0.0;
+        uint32_t keep = ne;
+        for (uint32_t i = 0; i < ne; i++) {
+          c += (double)buf[i].a;
+          if (c >= target) {
+            keep = i + 1;
+            break;
+          }
+        }
+        std::sort(buf, buf + keep, [](const Mss &x, const Mss &y) { return x.t < y.t; });
+        float lo = INFINITY, hi = -INFINITY;
+        size_t base = L.term.size();
+        for (uint32_t i = 0; i < keep; i++) {
+          float v;
+          std::memcpy(&v, &buf[i].i, 4);
+          L.term.push_back(buf[i].t);
+          L.val.push_back(v);
+          lo = std::min(lo, v);
+          hi = std::max(hi, v);
+        }
+        if (keep == 0) lo = hi = 0.0f;
+        float size = (float)(((double)hi - (double)lo) / 256.0);
+        L.m[g - g0] = lo;
+        L.size[g - g0] = size;
+        L.cnt[g - g0] = keep;
+        if (quant)
+          for (uint32_t i = 0; i < keep; i++) {
+            double q = size > 0.0f ? std::floor(((double)L.val[base + i] - (double)lo) / (double)size) : 0.0;
+            q = std::min(255.0, std::max(0.0, q));
+            L.code.push_back((uint8_t)q);
+          }
+      }
+    });
+  }
+  std::vector<uint32_t> sptr(nblk + 1, 0);
+  {
+    uint64_t acc = 0;
+    for (uint32_t t = 0; t < d; t++)
+      for (uint32_t b = 0; b < ls[t].cnt.size(); b++) {
+        sptr[bptr[t] + b] = (uint32_t)acc;
+        acc += ls[t].cnt[b];
+        if (acc > 0xFFFFFFFFull) return fail(SEISMIC_EINVAL, "more than 2^32 summary entries");
+      }
+    sptr[nblk] = (uint32_t)acc;
+    ix->n_sum = acc;
+  }
+  const uint64_t nsum = ix->n_sum;
+  {
+    std::vector<uint16_t> sterm(nsum);
+    std::vector<float> sval(nsum), bm(nblk), bsz(nblk);
+    std::vector<uint8_t> scode(quant ? nsum : 0);
+    std::vector<uint16_t> cblk(nsum);
+    std::vector<uint8_t> ccode(quant ? nsum : 0);
+    std::vector<float> cval(quant ? 0 : nsum);
+    const uint64_t stride = (uint64_t)d + 1;
+    std::unique_ptr<uint32_t[]> dir(new uint32_t[(size_t)d * stride]);
+    parallel_for(d, T, [&](int64_t t, int) {
+      const ListSum &L = ls[t];
+      uint32_t g0 = bptr[t], nb = bptr[t + 1] - g0;
+      uint32_t base = sptr[g0];
+      for (uint32_t b = 0; b < nb; b++) {
+        bm[g0 + b] = L.m[b];
+        bsz[g0 + b] = L.size[b];
+      }
+      if (!L.term.empty()) {
+        std::memcpy(&sterm[base], L.term.data(), L.term.size() * 2);
+        std::memcpy(&sval[base], L.val.data(), L.val.size() * 4);
+        if (quant) std::memcpy(&scode[base], L.code.data(), L.code.size());
+      }
+      // term-major layout of this list: columns by term, blocks ascending inside a column
+      uint32_t *dr = dir.get() + (size_t)t * stride;
+      std::fill(dr, dr + stride, 0u);
+      for (uint16_t s : L.term) dr[s + 1]++;
+      uint32_t run = base;
+      for (uint64_t s = 0; s <= d; s++) {
+        uint32_t c = (s < d) ? dr[s + 1] : 0;
+        dr[s] = run;
+        run += c;
+      }
+      std::vector<uint32_t> cur(dr, dr + d);
+      uint32_t e = 0;
+      for (uint32_t b = 0; b < nb; b++)
+        for (uint32_t i = 0; i < L.cnt[b]; i++, e++) {
+          uint32_t o = cur[L.term[e]]++;
+          cblk[o] = (uint16_t)b;
+          if (quant) ccode[o] = L.code[e];
+          else cval[o] = L.val[e];
+        }
+    });
+    if (ix->max_blocks_per_list > 65535) return fail(SEISMIC_EINVAL, "more than 65535 blocks in a list");
+    std::vector<ListSum>().swap(ls);
+    if ((rc = upload(ix->sum_ptr, sptr)) || (rc = upload(ix->sum_term, sterm)) || (rc = upload(ix->sum_val, sval)) ||
+        (rc = upload(ix->blk_m, bm)) || (rc = upload(ix->blk_size, bsz)) || (rc = upload(ix->scol_blk, cblk)))
+      return rc;
+    if (quant) {
+      if ((rc = upload(ix->sum_code, scode)) || (rc = upload(ix->scol_code, ccode))) return rc;
+    } else if ((rc = upload(ix->scol_val, cval))) {
+      return rc;
+    }
+    if ((rc = ix->sdir.alloc((size_t)d * stride * 4))) return rc;
+    SZ_CUDA(cudaMemcpy(ix->sdir.p, dir.get(), (size_t)d * stride * 4, cudaMemcpyHostToDevice));
+  }
+  if ((rc = upload(ix->list_ptr, lptr)) || (rc = upload(ix->list_doc, ldoc)) || (rc = upload(ix->cent, assign)) ||
+      (rc = upload(ix->blk_ptr, bptr)) || (rc = upload(ix->bdoc_ptr, bdptr)) || (rc = upload(ix->bdoc, bdoc)))
+    return rc;
+  SZ_CUDA(cudaDeviceSynchronize());
+  *out = ix.release();
+  return SEISMIC_OK;
+}
+
+}  // namespace seismic

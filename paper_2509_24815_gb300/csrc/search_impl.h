@@ -1,0 +1,78 @@
+// Launch arguments of the search kernels (internal).
+#pragma once
+
+#include "seismic_impl.h"
+
+namespace seismic {
+
+struct SearchArgs {
+  // index
+  const uint32_t *fwd_cptr;
+  const uint8_t *fwd_data;
+  const uint16_t *fwd_nnz;
+  const uint32_t *blk_ptr;
+  const uint32_t *bdoc_ptr;
+  const uint32_t *bdoc;
+  const float *blk_m;
+  const float *blk_size;
+  const uint32_t *sdir;
+  const uint16_t *scol_blk;
+  const uint8_t *scol_code;
+  const float *scol_val;
+  const uint32_t *knn;
+  uint32_t kappa;
+  uint32_t dim;
+  int quant;
+  // queries: CSR rows
+  const uint64_t *q_indptr;
+  const uint16_t *q_terms;
+  const float *q_vals;
+  uint32_t nq;
+  // parameters
+  uint32_t k, cut;
+  float hf;
+  int hf_mode, exhaustive, use_knn;
+  float alpha_q;
+  uint32_t wave;
+  const uint32_t *q_cut;  // learned per-query parameters, or NULL
+  const float *q_hf;
+  // outputs
+  uint32_t *ids;
+  float *scores;
+  unsigned long long *stats;
+  uint32_t *queue;  // [0] next query (persistent), [1] error bits
+  int persistent;
+  // shared-memory layout
+  uint32_t W, QN, BMAX, BPOW2, HS, CAND;
+  uint32_t off_qbits, off_qrank, off_qval, off_qterm, off_cut, off_aq, off_part, off_keys, off_clo, off_chi,
+      off_hash, off_tk_s, off_tk_id, off_tmp_s, off_tmp_id, off_cand_s, off_cand_id, off_cand_ok;
+};
+
+size_t search_layout(SearchArgs &a, uint32_t nw);
+int launch_search(const SearchArgs &a, uint32_t group, uint32_t nw, size_t smem, uint32_t grid, cudaStream_t st);
+int search_occupancy(uint32_t group, uint32_t nw, size_t smem, int *blocks);
+
+struct ExactArgs {
+  const uint32_t *full_ptr;
+  const uint32_t *full_doc;
+  const float *full_val;
+  uint32_t n_docs;
+  const uint64_t *q_indptr;
+  const uint16_t *q_terms;
+  const float *q_vals;
+  uint32_t nq;
+  uint32_t k;
+  float *acc;  // gridDim.x * n_docs floats, all zero between queries
+  uint32_t *ids;
+  float *scores;
+};
+int launch_exact(const ExactArgs &a, uint32_t grid, cudaStream_t st);
+constexpr uint32_t kExactMaxK = 1024;
+
+// MLP and features
+int launch_features(const uint64_t *q_indptr, const uint16_t *q_terms, const float *q_vals, uint32_t nq,
+                    const uint32_t *list_ptr, const uint32_t *blk_ptr, uint32_t dim, float *feat, cudaStream_t st);
+int launch_mlp_params(const float *w, const float *feat, uint32_t n, uint32_t cut_fallback, float hf_fallback,
+                      uint32_t *q_cut, float *q_hf, cudaStream_t st);
+
+}  // namespace seismic

@@ -1,0 +1,167 @@
+// Internal declarations of the Seismic GB300 library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <cstring>
+#include <functional>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/seismic.h"
+
+namespace seismic {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define SZ_CUDA(call)                                  \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+// ---------------------------------------------------------------- threads
+inline int hw_threads(int want) {
+  int n = (int)std::thread::hardware_concurrency();
+  if (n <= 0) n = 1;
+  return want > 0 ? want : n;
+}
+
+// Runs fn(i, tid) for i in [0, n) on `threads` workers pulling from a counter.
+inline void parallel_for(int64_t n, int threads, const std::function<void(int64_t, int)> &fn) {
+  if (threads <= 1 || n < 2) {
+    for (int64_t i = 0; i < n; i++) fn(i, 0);
+    return;
+  }
+  std::atomic<int64_t> next(0);
+  std::vector<std::thread> th;
+  for (int t = 0; t < threads; t++)
+    th.emplace_back([&, t] {
+      for (;;) {
+        int64_t i = next.fetch_add(1);
+        if (i >= n) break;
+        fn(i, t);
+      }
+    });
+  for (auto &x : th) x.join();
+}
+
+// ---------------------------------------------------------------- device memory
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  int alloc(size_t n) {  // SEISMIC_OK or SEISMIC_ENOMEM; contents undefined
+    release();
+    if (n == 0) n = 16;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      return fail(SEISMIC_ENOMEM, std::string("cudaMalloc of ") + std::to_string(n) + " bytes failed");
+    }
+    bytes = n;
+    return SEISMIC_OK;
+  }
+  int ensure(size_t n) { return n <= bytes && p ? SEISMIC_OK : alloc(n); }
+  template <class T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+template <class T> int upload(DevBuf &b, const std::vector<T> &v) {
+  int rc = b.alloc(v.size() * sizeof(T));
+  if (rc) return rc;
+  if (!v.empty()) SZ_CUDA(cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return SEISMIC_OK;
+}
+
+// Forward-index layout: each row is padded to a multiple of 8 entries and
+// stored as one 48-byte-aligned record: P u16 terms, then P fp32 values
+// (P = 8 * chunks).  Padding entries are (term 0, value 0), which add 0.
+constexpr uint32_t kChunk = 8;
+constexpr uint32_t kChunkBytes = 48;
+
+// Limits checked on the host before any device work.
+constexpr uint32_t kMaxRowNnzBuild = 8192;  // clustering stages a centroid chunk in shared memory
+constexpr uint32_t kMaxK = 1024;
+
+struct MlpState;
+
+}  // namespace seismic
+
+struct seismic_index {
+  int device = 0;
+  uint32_t dim = 0;
+  uint64_t n_docs = 0, nnz = 0, n_postings = 0, n_blocks = 0, n_sum = 0;
+  seismic_build_params bp{};
+  uint32_t max_blocks_per_list = 0;
+  uint32_t max_block_docs = 0;
+
+  // forward index
+  seismic::DevBuf fwd_cptr;  // u32[n_docs+1] row start in 8-entry chunks
+  seismic::DevBuf fwd_data;  // 48 bytes per chunk
+  seismic::DevBuf fwd_nnz;   // u16[n_docs] true nonzeros per row (work counters only)
+
+  // pruned lists, blocks
+  seismic::DevBuf list_ptr;  // u32[dim+1]
+  seismic::DevBuf list_doc;  // u32[n_postings]
+  seismic::DevBuf cent;      // u32[n_postings] cluster index per list position
+  seismic::DevBuf blk_ptr;   // u32[dim+1]
+  seismic::DevBuf bdoc_ptr;  // u32[n_blocks+1]
+  seismic::DevBuf bdoc;      // u32[n_postings]
+  seismic::DevBuf blk_m;     // f32[n_blocks]
+  seismic::DevBuf blk_size;  // f32[n_blocks]
+
+  // summaries, block-major (export / save)
+  seismic::DevBuf sum_ptr;   // u32[n_blocks+1]
+  seismic::DevBuf sum_term;  // u16[n_sum]
+  seismic::DevBuf sum_val;   // f32[n_sum]
+  seismic::DevBuf sum_code;  // u8[n_sum]
+
+  // summaries, term-major per list (search)
+  seismic::DevBuf sdir;      // u32[dim * (dim+1)]: column s of list t = [sdir[t*(dim+1)+s], +1)
+  seismic::DevBuf scol_blk;  // u16[n_sum] local block index
+  seismic::DevBuf scol_code; // u8[n_sum]
+  seismic::DevBuf scol_val;  // f32[n_sum] (fp32 summaries)
+
+  // unpruned lists for exact search
+  int has_full = 0;
+  seismic::DevBuf full_ptr;  // u32[dim+1]
+  seismic::DevBuf full_doc;  // u32[nnz]
+  seismic::DevBuf full_val;  // f32[nnz]
+
+  // kappa-NN graph
+  uint32_t kappa = 0;
+  seismic::DevBuf knn;       // u32[n_docs*kappa]
+
+  // MLP
+  int has_mlp = 0;
+  seismic::DevBuf mlp;       // f32[SEISMIC_MLP_PARAMS]
+
+  // search workspace (grown on demand)
+  seismic::DevBuf ws_q;      // staged host queries
+  seismic::DevBuf ws_out;    // staged outputs
+  seismic::DevBuf ws_stats;
+  seismic::DevBuf ws_queue;  // persistent-kernel work counter + error word
+  seismic::DevBuf ws_params; // per-query (cut, hf) for learned mode
+  seismic::DevBuf ws_feat;
+  seismic::DevBuf ws_exact;  // exact-search accumulators
+};
+
+namespace seismic {
+uint64_t device_bytes(const seismic_index *ix);
+int validate_host_csr(const seismic_csr *m, const char *what, uint32_t dim_expect);
+}  // namespace seismic
