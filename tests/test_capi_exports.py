@@ -14,8 +14,8 @@ HEADER = os.path.join(ROOT, "include", "seismic.h")
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_2509_24815_gb300 import build
-    path = build.build()
+    import __graft_entry__
+    path = __graft_entry__._builder().build()
     return ctypes.CDLL(path), path
 
 
