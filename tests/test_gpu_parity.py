@@ -451,12 +451,14 @@ def test_mlp_training_reduces_loss(sz, small, small_built):
     from oracle import mlp
     ix, _ = small_built[True]
     feat = torch.from_numpy(sz.seismic_query_features(ix, small["queries"])).cuda()
-    rng = np.random.default_rng(1)
-    t = torch.from_numpy(rng.random((feat.shape[0], 2)).astype(np.float32) * 0.5 + 0.25).cuda()
+    # learnable targets: a teacher network's outputs on the same features
+    teacher = mlp.init(7)
+    o, _ = mlp.forward(teacher, feat.cpu().numpy())
+    t = torch.from_numpy(mlp.sigmoid(o).astype(np.float32)).cuda()
     w = torch.from_numpy((mlp.init(2) * 0.3).astype(np.float32)).cuda()
     g, m, v, loss = torch.zeros_like(w), torch.zeros_like(w), torch.zeros_like(w), torch.zeros(1, device="cuda")
     losses = []
-    for step in range(1, 201):
+    for step in range(1, 401):
         sz.seismic_mlp_train_step(w, g, m, v, feat, t, 3e-3, step, loss)
         losses.append(loss.item())
     assert losses[-1] < 0.5 * losses[0], (losses[0], losses[-1])
