@@ -74,6 +74,8 @@ typedef struct {
   double beta_frac;      /* > 0: ceil(beta_frac * |list|) clusters per list; overrides beta */
   int32_t keep_full_lists; /* 1: also keep the unpruned lists for seismic_search_exact */
   int32_t threads;       /* host threads used by the build; 0 = all */
+  int32_t keep_block_summaries; /* 1: also keep the block-major summary arrays (SEISMIC_X_SUM_*);
+                                   search reads only the term-major copy */
 } seismic_build_params;
 
 /* Query processing (Algorithm "Query processing with Seismic", Section 4.5). */
@@ -190,7 +192,8 @@ enum {
   SEISMIC_X_BDOC,           /* uint32[n_postings]: members, ascending per block */
   SEISMIC_X_BLK_M,          /* float[n_blocks]: quantisation minimum m */
   SEISMIC_X_BLK_SIZE,       /* float[n_blocks]: quantisation sub-interval size */
-  SEISMIC_X_SUM_PTR,        /* uint32[n_blocks+1]: block-major summary entries */
+  SEISMIC_X_SUM_PTR,        /* uint32[n_blocks+1]: block-major summary entries (SUM_* need
+                               keep_block_summaries = 1) */
   SEISMIC_X_SUM_TERM,       /* uint16[n_summary_entries]: ascending per block */
   SEISMIC_X_SUM_VAL,        /* float[n_summary_entries]: max-summary values */
   SEISMIC_X_SUM_CODE,       /* uint8[n_summary_entries]: 8-bit codes */

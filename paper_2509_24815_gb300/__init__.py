@@ -49,7 +49,8 @@ class _CSR(ctypes.Structure):
 class BuildParams(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_uint32), ("beta", ctypes.c_uint32), ("alpha", ctypes.c_double),
                 ("quantize_u8", ctypes.c_int32), ("seed", ctypes.c_uint64), ("lambda_frac", ctypes.c_double),
-                ("beta_frac", ctypes.c_double), ("keep_full_lists", ctypes.c_int32), ("threads", ctypes.c_int32)]
+                ("beta_frac", ctypes.c_double), ("keep_full_lists", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("keep_block_summaries", ctypes.c_int32)]
 
 
 class SearchParams(ctypes.Structure):
@@ -177,11 +178,11 @@ class Index:
 
 
 def seismic_build(docs, lambda_=2000, beta=100, alpha=0.4, quantize_u8=False, seed=0, lambda_frac=0.0,
-                  beta_frac=0.0, keep_full_lists=False, threads=0) -> Index:
+                  beta_frac=0.0, keep_full_lists=False, threads=0, keep_block_summaries=False) -> Index:
     """Algorithm "Indexing with Seismic" on the current CUDA device."""
     s, keep = _csr_struct(docs)
     p = BuildParams(int(lambda_), int(beta), float(alpha), int(bool(quantize_u8)), int(seed), float(lambda_frac),
-                    float(beta_frac), int(bool(keep_full_lists)), int(threads))
+                    float(beta_frac), int(bool(keep_full_lists)), int(threads), int(bool(keep_block_summaries)))
     h = ctypes.c_void_p()
     _check(_lib.seismic_build(ctypes.byref(s), ctypes.byref(p), ctypes.byref(h)))
     return Index(h.value)

@@ -676,11 +676,15 @@ int build_index(const seismic_csr *docs, const seismic_build_params *bp, seismic
     });
     if (ix->max_blocks_per_list > 65535) return fail(SEISMIC_EINVAL, "more than 65535 blocks in a list");
     std::vector<ListSum>().swap(ls);
-    if ((rc = upload(ix->sum_ptr, sptr)) || (rc = upload(ix->sum_term, sterm)) || (rc = upload(ix->sum_val, sval)) ||
-        (rc = upload(ix->blk_m, bm)) || (rc = upload(ix->blk_size, bsz)) || (rc = upload(ix->scol_blk, cblk)))
+    if ((rc = upload(ix->blk_m, bm)) || (rc = upload(ix->blk_size, bsz)) || (rc = upload(ix->scol_blk, cblk)))
       return rc;
+    if (bp->keep_block_summaries) {
+      if ((rc = upload(ix->sum_ptr, sptr)) || (rc = upload(ix->sum_term, sterm)) || (rc = upload(ix->sum_val, sval)))
+        return rc;
+      if (quant && (rc = upload(ix->sum_code, scode))) return rc;
+    }
     if (quant) {
-      if ((rc = upload(ix->sum_code, scode)) || (rc = upload(ix->scol_code, ccode))) return rc;
+      if ((rc = upload(ix->scol_code, ccode))) return rc;
     } else if ((rc = upload(ix->scol_val, cval))) {
       return rc;
     }

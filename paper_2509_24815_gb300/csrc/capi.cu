@@ -221,9 +221,16 @@ int search_impl(seismic_index *ix, const seismic_csr *queries, const seismic_sea
                                      " B) exceeds 200 KB; lower hash_slots or the query size");
   uint32_t grid = nq;
   if (a.persistent) {
+    // persistent CTAs keep a seen bitmap of the collection each, in global
+    // memory (cleared per query), so deduplication never overflows
+    a.HS = 16;
+    smem = search_layout(a, nw);
     int blocks = 1;
     if ((rc = search_occupancy(group, nw, smem, &blocks))) return rc;
     grid = (uint32_t)std::min<uint64_t>(nq, (uint64_t)std::max(1, blocks) * sm_count(ix->device));
+    a.seen_words = (uint32_t)(((ix->n_docs + 31) / 32 + 3) & ~3ull);
+    if ((rc = ix->ws_seen.ensure((size_t)grid * a.seen_words * 4))) return rc;
+    a.seen_bm = ix->ws_seen.as<uint32_t>();
   }
   if ((rc = launch_search(a, group, nw, smem, grid, st))) return rc;
   if (!out_on_device) {
@@ -483,6 +490,7 @@ int export_impl(const seismic_index *ix, int32_t what, void *dst, uint64_t cap, 
     case SEISMIC_X_CENT: b = &ix->cent; n = ix->n_postings * 4; break;
     default: return fail(SEISMIC_EINVAL, "unknown export id");
   }
+  if (n && !b->p) return fail(SEISMIC_EINVAL, "array not kept: build with keep_block_summaries = 1");
   if (needed) *needed = n;
   if (!dst || cap < n || n == 0) return SEISMIC_OK;
   SZ_CUDA(cudaSetDevice(ix->device));

@@ -179,6 +179,7 @@ struct Smem {
   unsigned long long *keys;
   uint32_t *clo, *chi;
   uint32_t *hash;
+  uint32_t *seen;  // this CTA's global bitmap, or NULL
   float *tk_s, *tmp_s, *cand_s;
   uint32_t *tk_id, *tmp_id, *cand_id;
   uint8_t *cand_ok;
@@ -254,7 +255,14 @@ __device__ void eval_wave(const SearchArgs &a, Smem &s, Shared &sh, uint32_t n, 
     const uint32_t d = src(i);
     if (d == SEISMIC_NONE_ID) continue;
     uint32_t fresh = 0;
-    if (gl == 0) fresh = seen_insert(s.hash, a.HS - 1u, d, &sh.hash_full) ? 1u : 0u;
+    if (gl == 0) {
+      if (s.seen) {
+        const uint32_t bit = 1u << (d & 31);
+        fresh = (atomicOr(s.seen + (d >> 5), bit) & bit) ? 0u : 1u;
+      } else {
+        fresh = seen_insert(s.hash, a.HS - 1u, d, &sh.hash_full) ? 1u : 0u;
+      }
+    }
     fresh = __shfl_sync(gmask, fresh, 0, G);
     if (!fresh) continue;
     const float p = doc_dot<G>(a.fwd_data, a.fwd_cptr, d, gl, gmask, s.qbits, s.qrank, s.qval);
@@ -315,6 +323,7 @@ __global__ void __launch_bounds__(NW * 32) k_search(const SearchArgs a) {
   s.cand_s = reinterpret_cast<float *>(sm + a.off_cand_s);
   s.cand_id = reinterpret_cast<uint32_t *>(sm + a.off_cand_id);
   s.cand_ok = reinterpret_cast<uint8_t *>(sm + a.off_cand_ok);
+  s.seen = a.seen_bm ? a.seen_bm + (size_t)blockIdx.x * a.seen_words : nullptr;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   bool first = true;
 
@@ -332,7 +341,12 @@ __global__ void __launch_bounds__(NW * 32) k_search(const SearchArgs a) {
     const uint64_t qb = a.q_indptr[q], qe = a.q_indptr[q + 1];
     const uint32_t nnz = (uint32_t)(qe - qb);
     for (uint32_t i = tid; i < a.W; i += NT) s.qbits[i] = 0u;
-    for (uint32_t i = tid; i < a.HS; i += NT) s.hash[i] = 0u;
+    if (s.seen) {  // seen_words is a multiple of 4 and the slot is 16-byte aligned
+      uint4 *z = reinterpret_cast<uint4 *>(s.seen);
+      for (uint32_t i = tid; i < a.seen_words / 4; i += NT) z[i] = make_uint4(0u, 0u, 0u, 0u);
+    } else {
+      for (uint32_t i = tid; i < a.HS; i += NT) s.hash[i] = 0u;
+    }
     if (tid < SEISMIC_STATS_N) sh.st[tid] = 0ull;
     if (tid == 0) {
       sh.count = 0; sh.ncand = 0; sh.nvalid = 0; sh.hash_full = 0; sh.bad = 0;

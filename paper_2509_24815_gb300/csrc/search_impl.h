@@ -42,6 +42,10 @@ struct SearchArgs {
   unsigned long long *stats;
   uint32_t *queue;  // [0] next query (persistent), [1] error bits
   int persistent;
+  // seen set in global memory: one bitmap of seen_words words per CTA of a
+  // persistent launch (NULL: the bounded shared-memory hash set instead)
+  uint32_t *seen_bm;
+  uint32_t seen_words;
   // shared-memory layout
   uint32_t W, QN, BMAX, BPOW2, HS, CAND;
   uint32_t off_qbits, off_qrank, off_qval, off_qterm, off_cut, off_aq, off_part, off_keys, off_clo, off_chi,

@@ -159,6 +159,7 @@ struct seismic_index {
   seismic::DevBuf ws_params; // per-query (cut, hf) for learned mode
   seismic::DevBuf ws_feat;
   seismic::DevBuf ws_exact;  // exact-search accumulators
+  seismic::DevBuf ws_seen;   // per-CTA seen bitmaps of persistent searches
 };
 
 namespace seismic {

@@ -63,6 +63,7 @@ int main(void){
         sizeof(seismic_index_info));
  printf("%zu %zu %zu\n", offsetof(seismic_build_params, alpha), offsetof(seismic_build_params, lambda_frac),
         offsetof(seismic_search_params, hash_slots));
+ printf("%zu\n", offsetof(seismic_build_params, keep_block_summaries));
  return 0;}
 """
     tmp = os.path.join(ROOT, "_build_layout_probe")
@@ -76,4 +77,4 @@ int main(void){
     assert sizes[:4] == [ctypes.sizeof(sz._CSR), ctypes.sizeof(sz.BuildParams), ctypes.sizeof(sz.SearchParams),
                          ctypes.sizeof(sz.IndexInfo)]
     assert sizes[4:] == [sz.BuildParams.alpha.offset, sz.BuildParams.lambda_frac.offset,
-                         sz.SearchParams.hash_slots.offset]
+                         sz.SearchParams.hash_slots.offset, sz.BuildParams.keep_block_summaries.offset]

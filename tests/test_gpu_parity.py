@@ -55,7 +55,7 @@ def small_built(sz, small):
     out = {}
     for quant in (True, False):
         ix = sz.seismic_build(small["docs"], lambda_=small["lam"], beta=small["beta"], alpha=small["alpha"],
-                              quantize_u8=quant, seed=5, keep_full_lists=True)
+                              quantize_u8=quant, seed=5, keep_full_lists=True, keep_block_summaries=True)
         ox = oracle.Index(small["docs"], small["lam"], small["beta"], small["alpha"], quant, seed=5)
         out[quant] = (ix, ox)
     return out
@@ -68,7 +68,7 @@ def c1(sz):
     docs = synth.docs(100_000, seed=0)
     queries = synth.queries(1000, seed=0)
     ix = sz.seismic_build(docs, lambda_=2000, beta=100, alpha=0.4, quantize_u8=False, seed=0,
-                          keep_full_lists=True)
+                          keep_full_lists=True, keep_block_summaries=True)
     ox = oracle.Index(docs, 2000, 100, 0.4, False, seed=0)
     ei, es = oracle.exact_topk(docs, queries, 10)
     return dict(docs=docs, queries=queries, ix=ix, ox=ox, ei=ei, es=es)
