@@ -101,6 +101,10 @@ typedef struct {
                             inside stream capture).  Ignored for host queries. */
   uint32_t hash_slots;   /* per-query seen-set slots (power of two); 0 = 2048.  A full set only
                             costs repeated work, never a different result */
+  uint32_t shape;        /* 0 (auto): warp per query when k <= 128 and wave <= 1, else CTA per
+                            query; 1: one CTA per query (any k, any wave); 2: one warp per
+                            query (persistent, cta_warps independent warps per CTA: 1/2/4,
+                            0 = 4).  Both keep the algorithm's sequential order at wave 1 */
 } seismic_search_params;
 
 /* Per-query work counters written by seismic_search when `stats` is non-NULL:

@@ -632,6 +632,19 @@ int build_index(const seismic_csr *docs, const seismic_build_params *bp, seismic
     ix->n_sum = acc;
   }
   const uint64_t nsum = ix->n_sum;
+  {  // bound on |summary value| as the search reconstructs it (m + code * size)
+    double mx = 0.0;
+    for (uint32_t t = 0; t < d; t++) {
+      const ListSum &L = ls[t];
+      if (quant) {
+        for (size_t b = 0; b < L.m.size(); b++)
+          mx = std::max(mx, std::fabs((double)L.m[b]) + 256.0 * (double)L.size[b]);
+      } else {
+        for (float v : L.val) mx = std::max(mx, (double)std::fabs(v));
+      }
+    }
+    ix->sum_absmax = (float)(mx * 1.001 + 1e-30);
+  }
   {
     std::vector<uint16_t> sterm(nsum);
     std::vector<float> sval(nsum), bm(nblk), bsz(nblk);

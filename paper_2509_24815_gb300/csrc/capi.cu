@@ -120,8 +120,12 @@ int check_params(const seismic_index *ix, const seismic_search_params *p) {
   if (p->use_knn && ix->kappa == 0) return fail(SEISMIC_EINVAL, "use_knn: the index has no kappa-NN graph");
   if (p->learned && !ix->has_mlp) return fail(SEISMIC_EINVAL, "learned: the index has no MLP");
   uint32_t g = p->group ? p->group : 8, w = p->cta_warps ? p->cta_warps : 8;
-  if (!(g == 8 || g == 16 || g == 32) || !(w == 4 || w == 8 || w == 16))
-    return fail(SEISMIC_EINVAL, "group must be 8/16/32 and cta_warps 4/8/16");
+  if (p->shape > 2) return fail(SEISMIC_EINVAL, "shape must be 0 (auto), 1 (CTA per query) or 2 (warp per query)");
+  const bool ws = p->shape == 2 || (p->shape == 0 && p->k <= 128 && p->wave <= 1);
+  if (!(g == 8 || g == 16 || g == 32)) return fail(SEISMIC_EINVAL, "group must be 8/16/32");
+  const uint32_t ww = p->cta_warps ? p->cta_warps : 4;
+  if (ws ? !(ww == 1 || ww == 2 || ww == 4) : !(w == 4 || w == 8 || w == 16))
+    return fail(SEISMIC_EINVAL, "cta_warps must be 1/2/4 (warp shape) or 4/8/16 (CTA shape)");
   uint32_t hs = p->hash_slots ? p->hash_slots : 2048;
   if (hs & (hs - 1)) return fail(SEISMIC_EINVAL, "hash_slots must be a power of two");
   return SEISMIC_OK;
@@ -215,6 +219,26 @@ int search_impl(seismic_index *ix, const seismic_csr *queries, const seismic_sea
     a.QN = std::max<uint32_t>(a.QN, 32);
   }
   const uint32_t nw = p->cta_warps ? p->cta_warps : 8, group = p->group ? p->group : 8;
+  a.sum_absmax = ix->sum_absmax;
+  // shape: one warp per query (default when k <= 128 and wave = 1) or one CTA per query
+  const bool warp_shape = p->shape == 2 || (p->shape == 0 && k <= 128 && a.wave <= 1);
+  if (warp_shape) {
+    if (k > 128) return fail(SEISMIC_EINVAL, "the warp-per-query shape needs k <= 128");
+    const uint32_t wpb = p->cta_warps ? p->cta_warps : 4;
+    size_t wbytes = search_layout_warp(a);
+    size_t smem = wbytes * wpb;
+    if (smem > 200 * 1024)
+      return fail(SEISMIC_EBUDGET, "search: shared memory per CTA (" + std::to_string(smem) + " B) exceeds 200 KB");
+    int blocks = 1;
+    if ((rc = search_occupancy_warp(group, k, smem, wpb, &blocks))) return rc;
+    uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((nq + wpb - 1) / wpb,
+                                                                     (uint64_t)std::max(1, blocks) * sm_count(ix->device)));
+    a.seen_words = (uint32_t)(((ix->n_docs + 31) / 32 + 3) & ~3ull);
+    if ((rc = ix->ws_seen.ensure((size_t)grid * wpb * a.seen_words * 4))) return rc;
+    a.seen_bm = ix->ws_seen.as<uint32_t>();
+    a.persistent = 1;
+    if ((rc = launch_search_warp(a, group, smem, grid, wpb, st))) return rc;
+  } else {
   size_t smem = search_layout(a, nw);
   if (smem > 200 * 1024)
     return fail(SEISMIC_EBUDGET, "search: shared memory per query (" + std::to_string(smem) +
@@ -233,6 +257,7 @@ int search_impl(seismic_index *ix, const seismic_csr *queries, const seismic_sea
     a.seen_bm = ix->ws_seen.as<uint32_t>();
   }
   if ((rc = launch_search(a, group, nw, smem, grid, st))) return rc;
+  }
   if (!out_on_device) {
     SZ_CUDA(cudaMemcpyAsync(ids_out, d_ids, (size_t)nq * k * 4, cudaMemcpyDeviceToHost, st));
     SZ_CUDA(cudaMemcpyAsync(scores_out, d_sc, (size_t)nq * k * 4, cudaMemcpyDeviceToHost, st));
@@ -377,13 +402,14 @@ int build_knn_impl(seismic_index *ix, uint32_t kappa, const seismic_search_param
 // ---------------------------------------------------------------- persistence
 namespace {
 constexpr char kMagic[8] = {'S', 'E', 'I', 'S', 'M', 'I', 'C', '1'};
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 2;
 
 struct FileHead {
   char magic[8];
   uint32_t version, dim;
   uint64_t n_docs, nnz, n_postings, n_blocks, n_sum;
   uint32_t max_blocks_per_list, max_block_docs, kappa, has_full, has_mlp, quant;
+  float sum_absmax;
   seismic_build_params bp;
 };
 
@@ -417,6 +443,7 @@ int save_impl(const seismic_index *cix, const char *path) {
   h.has_full = ix->has_full;
   h.has_mlp = ix->has_mlp;
   h.quant = ix->bp.quantize_u8;
+  h.sum_absmax = ix->sum_absmax;
   h.bp = ix->bp;
   if (std::fwrite(&h, sizeof(h), 1, f.get()) != 1) return fail(SEISMIC_EIO, "write failed");
   std::vector<uint8_t> tmp;
@@ -454,6 +481,7 @@ int load_impl(const char *path, seismic_index **out) {
   ix->has_full = h.has_full;
   ix->has_mlp = h.has_mlp;
   ix->bp = h.bp;
+  ix->sum_absmax = h.sum_absmax;
   std::vector<uint8_t> tmp;
   for (int i = 0;; i++) {
     DevBuf *b = file_bufs(ix.get(), i);

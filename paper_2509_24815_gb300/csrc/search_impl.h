@@ -46,6 +46,10 @@ struct SearchArgs {
   // persistent launch (NULL: the bounded shared-memory hash set instead)
   uint32_t *seen_bm;
   uint32_t seen_words;
+  // warp-per-query kernel: shared-memory bytes per warp, and an upper bound
+  // on |summary value| (fixes the fixed-point scale of the summary scores)
+  uint32_t warp_bytes;
+  float sum_absmax;
   // shared-memory layout
   uint32_t W, QN, BMAX, BPOW2, HS, CAND;
   uint32_t off_qbits, off_qrank, off_qval, off_qterm, off_cut, off_aq, off_part, off_keys, off_clo, off_chi,
@@ -55,6 +59,10 @@ struct SearchArgs {
 size_t search_layout(SearchArgs &a, uint32_t nw);
 int launch_search(const SearchArgs &a, uint32_t group, uint32_t nw, size_t smem, uint32_t grid, cudaStream_t st);
 int search_occupancy(uint32_t group, uint32_t nw, size_t smem, int *blocks);
+size_t search_layout_warp(SearchArgs &a);
+int launch_search_warp(const SearchArgs &a, uint32_t group, size_t smem, uint32_t grid, uint32_t wpb,
+                       cudaStream_t st);
+int search_occupancy_warp(uint32_t group, uint32_t k, size_t smem, uint32_t wpb, int *blocks);
 
 struct ExactArgs {
   const uint32_t *full_ptr;

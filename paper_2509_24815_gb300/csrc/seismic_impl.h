@@ -109,6 +109,7 @@ struct seismic_index {
   seismic_build_params bp{};
   uint32_t max_blocks_per_list = 0;
   uint32_t max_block_docs = 0;
+  float sum_absmax = 0.0f;  // >= every |summary value| as the search dequantises it
 
   // forward index
   seismic::DevBuf fwd_cptr;  // u32[n_docs+1] row start in 8-entry chunks

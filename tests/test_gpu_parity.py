@@ -290,13 +290,53 @@ def test_exact_search_c1(sz, c1):
 
 
 # ------------------------------------------------------------------ launch variants
-@pytest.mark.parametrize("group,warps", [(8, 4), (16, 8), (32, 16), (8, 16)])
-def test_launch_shapes_agree(sz, small, small_built, group, warps):
+@pytest.mark.parametrize("shape,group,warps", [(1, 8, 4), (1, 16, 8), (1, 32, 16), (1, 8, 16), (2, 8, 1),
+                                               (2, 16, 4), (2, 32, 4), (2, 8, 2)])
+def test_launch_shapes_agree(sz, small, small_built, shape, group, warps):
     ix, _ = small_built[True]
     q = small["queries"]
-    a, sa = sz.seismic_search(ix, q, k=10, cut=5, heap_factor=0.8)
-    b, sb = sz.seismic_search(ix, q, k=10, cut=5, heap_factor=0.8, group=group, cta_warps=warps)
+    a, sa = sz.seismic_search(ix, q, k=10, cut=5, heap_factor=0.8, shape=1)
+    b, sb = sz.seismic_search(ix, q, k=10, cut=5, heap_factor=0.8, shape=shape, group=group, cta_warps=warps)
     check_exact_ids(small["docs"], q, b, sb, a, sa.astype(np.float64), tol=2e-5)
+
+
+@pytest.mark.parametrize("quant", [True, False])
+@pytest.mark.parametrize("k", [1, 10, 33, 100])
+def test_warp_shape_exhaustive_and_pruned(sz, small, small_built, quant, k):
+    """The warp-per-query kernel against the oracle: exhaustive ids/scores and
+    the same per-query work (blocks, documents) as the sequential algorithm."""
+    ix, ox = small_built[quant]
+    docs, queries = small["docs"], small["queries"]
+    gi, gs = sz.seismic_search(ix, queries, k=k, cut=5, exhaustive=True, shape=2)
+    ref = ox.search(queries, k, cut=5, exhaustive=True)
+    check_exact_ids(docs, queries, gi, gs, ref["ids"], ref["scores"])
+    gi, gs, st = sz.seismic_search(ix, queries, k=k, cut=5, heap_factor=0.9, shape=2, stats=True)
+    ref = ox.search(queries, k, cut=5, heap_factor=f32(0.9))
+    same_docs = (st[:, sz.STATS.index("docs")] == ref["stats"][:, 4]).mean()
+    same_blocks = (st[:, sz.STATS.index("blocks_evaluated")] == ref["stats"][:, 2]).mean()
+    assert same_blocks >= 0.97 and same_docs >= 0.97, (same_blocks, same_docs)
+    ei, es = oracle.exact_topk(docs, queries, k)
+    if k >= 10:
+        rg = oracle.recall_at_k(docs, queries, gi, es, 10).mean()
+        ro = oracle.recall_at_k(docs, queries, ref["ids"], es, 10).mean()
+        assert abs(rg - ro) <= 0.005, (rg, ro)
+    check_scores_only(docs, queries, gi, gs)
+
+
+def test_warp_shape_knn_and_alpha_q(sz, small, small_built):
+    ix, ox = small_built[True]
+    docs, queries = small["docs"], small["queries"]
+    knn = oracle.knn_exact(docs, 8)
+    sz.seismic_set_knn(ix, knn)
+    ei, es = oracle.exact_topk(docs, queries, 10)
+    gi, gs = sz.seismic_search(ix, queries, k=10, cut=2, heap_factor=0.9, use_knn=True, shape=2)
+    ref = ox.search(queries, 10, cut=2, heap_factor=f32(0.9), knn=knn)
+    assert abs(oracle.recall_at_k(docs, queries, gi, es, 10).mean()
+               - oracle.recall_at_k(docs, queries, ref["ids"], es, 10).mean()) <= 0.005
+    check_scores_only(docs, queries, gi, gs)
+    gi, _, st = sz.seismic_search(ix, queries, k=10, alpha_q=0.4, heap_factor=0.9, shape=2, stats=True)
+    ref = ox.search(queries, 10, alpha_q=f32(0.4), heap_factor=f32(0.9))
+    np.testing.assert_array_equal(st[:, 0], ref["stats"][:, 0])
 
 
 def test_persistent_equals_plain(sz, small, small_built):
