@@ -313,7 +313,7 @@ int validate_host_csr(const seismic_csr *m, const char *what, uint32_t dim_expec
 
 uint64_t device_bytes(const seismic_index *ix) {
   const DevBuf *b[] = {&ix->fwd_cptr, &ix->fwd_data, &ix->fwd_nnz, &ix->list_ptr, &ix->list_doc, &ix->cent,
-                       &ix->blk_ptr, &ix->bdoc_ptr, &ix->bdoc, &ix->blk_m, &ix->blk_size, &ix->sum_ptr,
+                       &ix->blk_ptr, &ix->bdoc_ptr, &ix->bdoc, &ix->bdoc_row, &ix->blk_m, &ix->blk_size, &ix->sum_ptr,
                        &ix->sum_term, &ix->sum_val, &ix->sum_code, &ix->sdir, &ix->scol_blk, &ix->scol_code,
                        &ix->scol_val, &ix->full_ptr, &ix->full_doc, &ix->full_val, &ix->knn, &ix->mlp};
   uint64_t s = 0;
@@ -340,8 +340,8 @@ int build_index(const seismic_csr *docs, const seismic_build_params *bp, seismic
   ix->bp = *bp;
 
   // ---- forward index, padded 8-entry chunks
+  std::vector<uint32_t> cptr(D.n + 1, 0);
   {
-    std::vector<uint32_t> cptr(D.n + 1, 0);
     std::vector<uint16_t> rnnz(D.n);
     for (uint64_t i = 0; i < D.n; i++) {
       uint64_t n = D.ip[i + 1] - D.ip[i];
@@ -707,6 +707,14 @@ int build_index(const seismic_csr *docs, const seismic_build_params *bp, seismic
   if ((rc = upload(ix->list_ptr, lptr)) || (rc = upload(ix->list_doc, ldoc)) || (rc = upload(ix->cent, assign)) ||
       (rc = upload(ix->blk_ptr, bptr)) || (rc = upload(ix->bdoc_ptr, bdptr)) || (rc = upload(ix->bdoc, bdoc)))
     return rc;
+  {  // each member's forward row (first chunk, chunk count) beside its id: one dependent load fewer
+    std::vector<uint64_t> brow(npost);
+    parallel_for((int64_t)npost, T, [&](int64_t p, int) {
+      const uint32_t j = bdoc[p];
+      brow[p] = (uint64_t)cptr[j] | ((uint64_t)(cptr[j + 1] - cptr[j]) << 32);
+    });
+    if ((rc = upload(ix->bdoc_row, brow))) return rc;
+  }
   SZ_CUDA(cudaDeviceSynchronize());
   *out = ix.release();
   return SEISMIC_OK;

@@ -167,6 +167,7 @@ int search_impl(seismic_index *ix, const seismic_csr *queries, const seismic_sea
   a.blk_ptr = ix->blk_ptr.as<uint32_t>();
   a.bdoc_ptr = ix->bdoc_ptr.as<uint32_t>();
   a.bdoc = ix->bdoc.as<uint32_t>();
+  a.bdoc_row = ix->bdoc_row.as<unsigned long long>();
   a.blk_m = ix->blk_m.as<float>();
   a.blk_size = ix->blk_size.as<float>();
   a.sdir = ix->sdir.as<uint32_t>();
@@ -415,7 +416,7 @@ struct FileHead {
 
 DevBuf *file_bufs(seismic_index *ix, int i) {
   DevBuf *b[] = {&ix->fwd_cptr, &ix->fwd_data, &ix->fwd_nnz, &ix->list_ptr, &ix->list_doc, &ix->cent, &ix->blk_ptr,
-                 &ix->bdoc_ptr, &ix->bdoc, &ix->blk_m, &ix->blk_size, &ix->sum_ptr, &ix->sum_term, &ix->sum_val,
+                 &ix->bdoc_ptr, &ix->bdoc, &ix->bdoc_row, &ix->blk_m, &ix->blk_size, &ix->sum_ptr, &ix->sum_term, &ix->sum_val,
                  &ix->sum_code, &ix->sdir, &ix->scol_blk, &ix->scol_code, &ix->scol_val, &ix->full_ptr,
                  &ix->full_doc, &ix->full_val, &ix->knn, &ix->mlp};
   return i < (int)(sizeof(b) / sizeof(b[0])) ? b[i] : nullptr;

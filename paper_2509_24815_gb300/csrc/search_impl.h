@@ -13,6 +13,7 @@ struct SearchArgs {
   const uint32_t *blk_ptr;
   const uint32_t *bdoc_ptr;
   const uint32_t *bdoc;
+  const unsigned long long *bdoc_row;  // member's forward row: first chunk | chunks << 32
   const float *blk_m;
   const float *blk_size;
   const uint32_t *sdir;

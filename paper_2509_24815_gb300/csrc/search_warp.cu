@@ -59,42 +59,38 @@ template <int G>
 __device__ __forceinline__ float row_dot(const uint8_t *__restrict__ fwd, uint32_t c0, uint32_t nch, int gl,
                                          uint32_t gmask, const uint32_t *__restrict__ qbits,
                                          const uint16_t *__restrict__ qrank, const float *__restrict__ qval) {
+  // a lane takes chunks gl, gl + G, ... and keeps U of them (48 bytes each) in
+  // flight at once; products are added in chunk order, so U never changes a sum
+  constexpr int U = G >= 16 ? 2 : 16 / G;
   const uint8_t *rec = fwd + (size_t)c0 * 48;
   const uint8_t *vrec = rec + 16 * (size_t)nch;
   float acc = 0.0f;
-  uint32_t c = gl;
 #pragma unroll 1
-  for (; c + G < nch; c += 2 * G) {
-    const uint4 t0 = ldg_na(rec + 16 * (size_t)c);
-    const uint4 a0 = ldg_na(vrec + 32 * (size_t)c);
-    const uint4 b0 = ldg_na(vrec + 32 * (size_t)c + 16);
-    const uint4 t1 = ldg_na(rec + 16 * (size_t)(c + G));
-    const uint4 a1 = ldg_na(vrec + 32 * (size_t)(c + G));
-    const uint4 b1 = ldg_na(vrec + 32 * (size_t)(c + G) + 16);
-    const uint32_t tw0[4] = {t0.x, t0.y, t0.z, t0.w}, tw1[4] = {t1.x, t1.y, t1.z, t1.w};
-    const uint32_t va0[8] = {a0.x, a0.y, a0.z, a0.w, b0.x, b0.y, b0.z, b0.w};
-    const uint32_t va1[8] = {a1.x, a1.y, a1.z, a1.w, b1.x, b1.y, b1.z, b1.w};
+  for (uint32_t c = gl; c < nch; c += U * G) {
+    uint4 t[U], va[U], vb[U];
 #pragma unroll
-    for (int e = 0; e < 4; e++) {
-      acc = fmaf(qlookup(qbits, qrank, qval, tw0[e] & 0xFFFFu), __uint_as_float(va0[2 * e]), acc);
-      acc = fmaf(qlookup(qbits, qrank, qval, tw0[e] >> 16), __uint_as_float(va0[2 * e + 1]), acc);
+    for (int u = 0; u < U; u++) {
+      const uint32_t cc = c + u * G;
+      if (cc < nch) {
+        t[u] = ldg_na(rec + 16 * (size_t)cc);
+        va[u] = ldg_na(vrec + 32 * (size_t)cc);
+        vb[u] = ldg_na(vrec + 32 * (size_t)cc + 16);
+      } else {
+        t[u] = make_uint4(0u, 0u, 0u, 0u);
+        va[u] = t[u];
+        vb[u] = t[u];
+      }
     }
 #pragma unroll
-    for (int e = 0; e < 4; e++) {
-      acc = fmaf(qlookup(qbits, qrank, qval, tw1[e] & 0xFFFFu), __uint_as_float(va1[2 * e]), acc);
-      acc = fmaf(qlookup(qbits, qrank, qval, tw1[e] >> 16), __uint_as_float(va1[2 * e + 1]), acc);
-    }
-  }
-  if (c < nch) {
-    const uint4 t0 = ldg_na(rec + 16 * (size_t)c);
-    const uint4 a0 = ldg_na(vrec + 32 * (size_t)c);
-    const uint4 b0 = ldg_na(vrec + 32 * (size_t)c + 16);
-    const uint32_t tw0[4] = {t0.x, t0.y, t0.z, t0.w};
-    const uint32_t va0[8] = {a0.x, a0.y, a0.z, a0.w, b0.x, b0.y, b0.z, b0.w};
+    for (int u = 0; u < U; u++) {
+      if (c + u * G >= nch) break;
+      const uint32_t tw[4] = {t[u].x, t[u].y, t[u].z, t[u].w};
+      const uint32_t vv[8] = {va[u].x, va[u].y, va[u].z, va[u].w, vb[u].x, vb[u].y, vb[u].z, vb[u].w};
 #pragma unroll
-    for (int e = 0; e < 4; e++) {
-      acc = fmaf(qlookup(qbits, qrank, qval, tw0[e] & 0xFFFFu), __uint_as_float(va0[2 * e]), acc);
-      acc = fmaf(qlookup(qbits, qrank, qval, tw0[e] >> 16), __uint_as_float(va0[2 * e + 1]), acc);
+      for (int e = 0; e < 4; e++) {
+        acc = fmaf(qlookup(qbits, qrank, qval, tw[e] & 0xFFFFu), __uint_as_float(vv[2 * e]), acc);
+        acc = fmaf(qlookup(qbits, qrank, qval, tw[e] >> 16), __uint_as_float(vv[2 * e + 1]), acc);
+      }
     }
   }
 #pragma unroll
@@ -178,7 +174,29 @@ struct WarpCounters {
   unsigned long long v[SEISMIC_STATS_N];
 };
 
-// Scores documents src(0..n) (uniform n), offering each to the top-k.
+// Document sources: src.id(i) and src.row(i) = first chunk | chunks << 32.
+struct MemberSrc {  // the members of a block (ids and their rows side by side)
+  const uint32_t *ids;
+  const unsigned long long *rows;
+  __device__ __forceinline__ uint32_t id(uint32_t i) const { return __ldg(ids + i); }
+  __device__ __forceinline__ unsigned long long row(uint32_t i, uint32_t) const { return __ldg(rows + i); }
+};
+struct GraphSrc {  // the kappa-NN neighbours of S
+  const uint32_t *S, *knn, *cptr;
+  uint32_t kappa;
+  __device__ __forceinline__ uint32_t id(uint32_t x) const {
+    return __ldg(knn + (size_t)S[x / kappa] * kappa + (x % kappa));
+  }
+  __device__ __forceinline__ unsigned long long row(uint32_t, uint32_t d) const {
+    if (d == SEISMIC_NONE_ID) return 0ull;
+    const uint32_t c0 = __ldg(cptr + d);
+    return (unsigned long long)c0 | ((unsigned long long)(__ldg(cptr + d + 1) - c0) << 32);
+  }
+};
+
+// Scores documents 0..n of src (n uniform over the warp), offering each new
+// one to the top-k.  The seen-bitmap test is issued together with the row's
+// loads; a document already seen is scored and dropped.
 template <int G, int R, class Src>
 __device__ void eval_docs(const SearchArgs &a, const WarpSmem &s, uint32_t *seen, TopK<R> &tk, uint32_t n, Src src,
                           int lane, WarpCounters &st, int knn_stage) {
@@ -187,24 +205,24 @@ __device__ void eval_docs(const SearchArgs &a, const WarpSmem &s, uint32_t *seen
   const uint32_t gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
   for (uint32_t base = 0; base < n; base += NG) {
     const uint32_t i = base + grp;
-    uint32_t d = SEISMIC_NONE_ID, fresh = 0u, c0 = 0u, nch = 0u;
+    uint32_t d = SEISMIC_NONE_ID, old = 0u, bit = 0u;
+    unsigned long long row = 0ull;
     if (i < n) {
-      d = src(i);
-      if (gl == 0 && d != SEISMIC_NONE_ID) {
-        const uint32_t bit = 1u << (d & 31);
-        fresh = (atomicOr(seen + (d >> 5), bit) & bit) ? 0u : 1u;
+      d = src.id(i);
+      row = src.row(i, d);  // for block members this load does not wait for d
+      if (d != SEISMIC_NONE_ID) {
+        bit = 1u << (d & 31);
+        if (gl == 0) old = atomicOr(seen + (d >> 5), bit);
       }
     }
-    fresh = __shfl_sync(0xffffffffu, fresh, grp * G);
     float p = -INFINITY;
-    if (fresh) {
-      c0 = __ldg(a.fwd_cptr + d);
-      nch = __ldg(a.fwd_cptr + d + 1) - c0;
-      p = row_dot<G>(a.fwd_data, c0, nch, gl, gmask, s.qbits, s.qrank, s.qval);
-      if (a.stats && gl == 0) {
-        st.v[knn_stage ? SEISMIC_ST_KNN_DOCS : SEISMIC_ST_DOCS]++;
-        st.v[knn_stage ? SEISMIC_ST_KNN_NNZ : SEISMIC_ST_DOC_NNZ] += a.fwd_nnz[d];
-      }
+    if (d != SEISMIC_NONE_ID)
+      p = row_dot<G>(a.fwd_data, (uint32_t)row, (uint32_t)(row >> 32), gl, gmask, s.qbits, s.qrank, s.qval);
+    uint32_t fresh = (d != SEISMIC_NONE_ID && !(old & bit)) ? 1u : 0u;
+    fresh = __shfl_sync(0xffffffffu, fresh, grp * G);
+    if (fresh && a.stats && gl == 0) {
+      st.v[knn_stage ? SEISMIC_ST_KNN_DOCS : SEISMIC_ST_DOCS]++;
+      st.v[knn_stage ? SEISMIC_ST_KNN_NNZ : SEISMIC_ST_DOC_NNZ] += a.fwd_nnz[d];
     }
 #pragma unroll
     for (int g = 0; g < NG; g++) {
@@ -375,8 +393,8 @@ __global__ void __launch_bounds__(128, 5) k_search_warp(const SearchArgs a) {
             st.v[SEISMIC_ST_BLOCKS_EVALUATED] += nb;
             st.v[SEISMIC_ST_BLOCK_DOCS] += d1 - d0;
           }
-          const uint32_t *src = a.bdoc + d0;
-          eval_docs<G, R>(a, s, seen, tk, d1 - d0, [src](uint32_t i) { return __ldg(src + i); }, lane, st, 0);
+          const MemberSrc src{a.bdoc + d0, a.bdoc_row + d0};
+          eval_docs<G, R>(a, s, seen, tk, d1 - d0, src, lane, st, 0);
           continue;
         }
         // ---- H2: column ranges, flat offsets, fixed-point scores
@@ -462,8 +480,8 @@ __global__ void __launch_bounds__(128, 5) k_search_warp(const SearchArgs a) {
             st.v[SEISMIC_ST_BLOCKS_EVALUATED]++;
             st.v[SEISMIC_ST_BLOCK_DOCS] += d1 - d0;
           }
-          const uint32_t *src = a.bdoc + d0;
-          eval_docs<G, R>(a, s, seen, tk, d1 - d0, [src](uint32_t i) { return __ldg(src + i); }, lane, st, 0);
+          const MemberSrc src{a.bdoc + d0, a.bdoc_row + d0};
+          eval_docs<G, R>(a, s, seen, tk, d1 - d0, src, lane, st, 0);
         }
         __syncwarp();
       }
@@ -477,11 +495,8 @@ __global__ void __launch_bounds__(128, 5) k_search_warp(const SearchArgs a) {
           if (e < ns) S[e] = tk.id[r];
         }
         __syncwarp();
-        const uint32_t *knn = a.knn;
-        const uint32_t kappa = a.kappa;
-        eval_docs<G, R>(a, s, seen, tk, ns * kappa,
-                        [S, knn, kappa](uint32_t x) { return __ldg(knn + (size_t)S[x / kappa] * kappa + (x % kappa)); },
-                        lane, st, 1);
+        const GraphSrc src{S, a.knn, a.fwd_cptr, a.kappa};
+        eval_docs<G, R>(a, s, seen, tk, ns * a.kappa, src, lane, st, 1);
       }
       // ------------------------------------------------------ output
 #pragma unroll
@@ -554,22 +569,24 @@ int launch_search_warp(const SearchArgs &a, uint32_t group, size_t smem, uint32_
   const uint32_t R = (a.k + 31) / 32;
 #define SZ_CASE(G_, R_) \
   if (group == G_ && R <= R_) return launch_w<G_, R_>(a, smem, grid, wpb, st);
+  SZ_CASE(4, 1) SZ_CASE(4, 2) SZ_CASE(4, 4)
   SZ_CASE(8, 1) SZ_CASE(8, 2) SZ_CASE(8, 4)
   SZ_CASE(16, 1) SZ_CASE(16, 2) SZ_CASE(16, 4)
   SZ_CASE(32, 1) SZ_CASE(32, 2) SZ_CASE(32, 4)
 #undef SZ_CASE
-  return fail(SEISMIC_EINVAL, "warp search: group must be 8/16/32 and k <= 128");
+  return fail(SEISMIC_EINVAL, "warp search: group must be 4/8/16/32 and k <= 128");
 }
 
 int search_occupancy_warp(uint32_t group, uint32_t k, size_t smem, uint32_t wpb, int *blocks) {
   const uint32_t R = (k + 31) / 32;
 #define SZ_CASE(G_, R_) \
   if (group == G_ && R <= R_) return occ_w<G_, R_>(smem, wpb, blocks);
+  SZ_CASE(4, 1) SZ_CASE(4, 2) SZ_CASE(4, 4)
   SZ_CASE(8, 1) SZ_CASE(8, 2) SZ_CASE(8, 4)
   SZ_CASE(16, 1) SZ_CASE(16, 2) SZ_CASE(16, 4)
   SZ_CASE(32, 1) SZ_CASE(32, 2) SZ_CASE(32, 4)
 #undef SZ_CASE
-  return fail(SEISMIC_EINVAL, "warp search: group must be 8/16/32 and k <= 128");
+  return fail(SEISMIC_EINVAL, "warp search: group must be 4/8/16/32 and k <= 128");
 }
 
 }  // namespace seismic

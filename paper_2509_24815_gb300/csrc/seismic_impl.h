@@ -123,6 +123,7 @@ struct seismic_index {
   seismic::DevBuf blk_ptr;   // u32[dim+1]
   seismic::DevBuf bdoc_ptr;  // u32[n_blocks+1]
   seismic::DevBuf bdoc;      // u32[n_postings]
+  seismic::DevBuf bdoc_row;  // u64[n_postings]: member's forward row, first chunk | chunks << 32
   seismic::DevBuf blk_m;     // f32[n_blocks]
   seismic::DevBuf blk_size;  // f32[n_blocks]
 

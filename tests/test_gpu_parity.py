@@ -291,7 +291,7 @@ def test_exact_search_c1(sz, c1):
 
 # ------------------------------------------------------------------ launch variants
 @pytest.mark.parametrize("shape,group,warps", [(1, 8, 4), (1, 16, 8), (1, 32, 16), (1, 8, 16), (2, 8, 1),
-                                               (2, 16, 4), (2, 32, 4), (2, 8, 2)])
+                                               (2, 16, 4), (2, 32, 4), (2, 8, 2), (2, 4, 4), (2, 4, 1)])
 def test_launch_shapes_agree(sz, small, small_built, shape, group, warps):
     ix, _ = small_built[True]
     q = small["queries"]
