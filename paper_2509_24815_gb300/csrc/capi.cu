@@ -122,7 +122,8 @@ int check_params(const seismic_index *ix, const seismic_search_params *p) {
   uint32_t g = p->group ? p->group : 8, w = p->cta_warps ? p->cta_warps : 8;
   if (p->shape > 2) return fail(SEISMIC_EINVAL, "shape must be 0 (auto), 1 (CTA per query) or 2 (warp per query)");
   const bool ws = p->shape == 2 || (p->shape == 0 && p->k <= 128 && p->wave <= 1);
-  if (!(g == 8 || g == 16 || g == 32)) return fail(SEISMIC_EINVAL, "group must be 8/16/32");
+  if (!(g == 8 || g == 16 || g == 32 || (ws && g == 4)))
+    return fail(SEISMIC_EINVAL, "group must be 8/16/32 (4 also for the warp shape)");
   const uint32_t ww = p->cta_warps ? p->cta_warps : 4;
   if (ws ? !(ww == 1 || ww == 2 || ww == 4) : !(w == 4 || w == 8 || w == 16))
     return fail(SEISMIC_EINVAL, "cta_warps must be 1/2/4 (warp shape) or 4/8/16 (CTA shape)");
@@ -221,6 +222,7 @@ int search_impl(seismic_index *ix, const seismic_csr *queries, const seismic_sea
   }
   const uint32_t nw = p->cta_warps ? p->cta_warps : 8, group = p->group ? p->group : 8;
   a.sum_absmax = ix->sum_absmax;
+  a.prefetch = p->no_prefetch ? 0u : 256u;
   // shape: one warp per query (default when k <= 128 and wave = 1) or one CTA per query
   const bool warp_shape = p->shape == 2 || (p->shape == 0 && k <= 128 && a.wave <= 1);
   if (warp_shape) {

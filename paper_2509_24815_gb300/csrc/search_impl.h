@@ -51,6 +51,7 @@ struct SearchArgs {
   // on |summary value| (fixes the fixed-point scale of the summary scores)
   uint32_t warp_bytes;
   float sum_absmax;
+  uint32_t prefetch;  // rows of the next block prefetched into L2 (at most this many; 0 = off)
   // shared-memory layout
   uint32_t W, QN, BMAX, BPOW2, HS, CAND;
   uint32_t off_qbits, off_qrank, off_qval, off_qterm, off_cut, off_aq, off_part, off_keys, off_clo, off_chi,

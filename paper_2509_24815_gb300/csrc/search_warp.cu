@@ -47,6 +47,15 @@ __device__ __forceinline__ float qlookup(const uint32_t *__restrict__ qbits, con
   if (!(w & bit)) return 0.0f;
   return qval[qrank[t >> 5] + __popc(w & (bit - 1u))];
 }
+// TMA bulk prefetch of [p, p + bytes) into L2 (no registers, no completion):
+// p is rounded down and the end up to 16-byte boundaries; allocations carry
+// 256 bytes of slack, so the rounded range stays inside them.
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p), lo = a & ~(uintptr_t)15;
+  const uint32_t n = (uint32_t)(((a + bytes + 15) & ~(uintptr_t)15) - lo);
+  if (n) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"(n) : "memory");
+}
+
 __device__ __forceinline__ uint4 ldg_na(const void *p) {
   uint4 r;
   asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
@@ -463,7 +472,29 @@ __global__ void __launch_bounds__(128, 5) k_search_warp(const SearchArgs a) {
             }
             __syncwarp();
           }
-        // ---- H4-H6: visit blocks
+        // ---- H4-H6: visit blocks.  While block bi is scored, the member
+        // lists of block bi+2 and the rows of block bi+1 are prefetched into L2
+        // (speculatively: a skip ends the list, wasting at most two blocks).
+        const uint32_t pf = a.prefetch;
+        auto members_l2 = [&](uint32_t bj) {
+          if (!pf || bj >= nb || lane != 0) return;
+          const uint32_t bb = (uint32_t)(s.rk[bj] & 0xFFFFFFFFu);
+          const uint32_t e0 = __ldg(a.bdoc_ptr + g0 + bb), e1 = __ldg(a.bdoc_ptr + g0 + bb + 1);
+          prefetch_l2(a.bdoc + e0, 4 * (e1 - e0));
+          prefetch_l2(a.bdoc_row + e0, 8 * (e1 - e0));
+        };
+        auto rows_l2 = [&](uint32_t bj) {
+          if (!pf || bj >= nb) return;
+          const uint32_t bb = (uint32_t)(s.rk[bj] & 0xFFFFFFFFu);
+          const uint32_t e0 = __ldg(a.bdoc_ptr + g0 + bb), e1 = min(__ldg(a.bdoc_ptr + g0 + bb + 1), e0 + pf);
+          for (uint32_t e = e0 + lane; e < e1; e += 32) {
+            const unsigned long long row = __ldg(a.bdoc_row + e);
+            prefetch_l2(a.fwd_data + (size_t)(uint32_t)row * 48, 48u * (uint32_t)(row >> 32));
+          }
+        };
+        members_l2(0);
+        members_l2(1);
+        rows_l2(0);
         for (uint32_t bi = 0; bi < nb; bi++) {
           const unsigned long long key = s.rk[bi];
           if (tk.count == a.k) {
@@ -480,6 +511,8 @@ __global__ void __launch_bounds__(128, 5) k_search_warp(const SearchArgs a) {
             st.v[SEISMIC_ST_BLOCKS_EVALUATED]++;
             st.v[SEISMIC_ST_BLOCK_DOCS] += d1 - d0;
           }
+          members_l2(bi + 2);
+          rows_l2(bi + 1);
           const MemberSrc src{a.bdoc + d0, a.bdoc_row + d0};
           eval_docs<G, R>(a, s, seen, tk, d1 - d0, src, lane, st, 0);
         }

@@ -67,8 +67,9 @@ struct DevBuf {
   }
   int alloc(size_t n) {  // SEISMIC_OK or SEISMIC_ENOMEM; contents undefined
     release();
-    if (n == 0) n = 16;
-    cudaError_t e = cudaMalloc(&p, n);
+    // 256 bytes of slack: readers may round a range out to 16-byte boundaries
+    // (bulk L2 prefetches), which must stay inside the allocation
+    cudaError_t e = cudaMalloc(&p, n + 256);
     if (e != cudaSuccess) {
       p = nullptr;
       cudaGetLastError();
