@@ -177,9 +177,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--group", type=int, default=8)
-    ap.add_argument("--cta-warps", type=int, default=8)
-    ap.add_argument("--wave", type=int, default=1)
+    ap.add_argument("--cta-warps", type=int, default=0)
+    ap.add_argument("--wave", type=int, default=16)
     ap.add_argument("--persistent", type=int, default=1)
+    ap.add_argument("--shape", type=int, default=1, help="1: CTA per query, 2: warp per query, 0: auto")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -228,7 +229,7 @@ def main():
     def params(cut, hf):
         return sz.search_params(k=K, cut=cut, heap_factor=hf, use_knn=bool(w["kappa"]), wave=args.wave,
                                 group=args.group, cta_warps=args.cta_warps, persistent=bool(args.persistent),
-                                max_query_nnz=dq.max_row_nnz)
+                                max_query_nnz=dq.max_row_nnz, shape=args.shape)
 
     def run(p):
         sz.seismic_search(ix, dq, p, ids_out=ids, scores_out=sc, stream=stream)
@@ -289,7 +290,7 @@ def main():
     hsc = torch.empty((queries.n_rows, K), dtype=torch.float32).pin_memory()
     pe = sz.search_params(k=K, cut=best["cut"], heap_factor=best["heap_factor"], use_knn=bool(w["kappa"]),
                           wave=args.wave, group=args.group, cta_warps=args.cta_warps,
-                          persistent=bool(args.persistent))
+                          persistent=bool(args.persistent), shape=args.shape)
     for _ in range(2):
         sz.seismic_search(ix, hq, pe, ids_out=hid, scores_out=hsc, stream=stream)
     e2e_t = []
@@ -312,6 +313,7 @@ def main():
                    "recall@10": best["recall"], "queries_per_step": dq.n_rows, "k": K,
                    "l2": "index resident in HBM, larger than L2 (no flush)", "group": args.group,
                    "cta_warps": args.cta_warps, "wave": args.wave, "persistent": args.persistent,
+                   "shape": args.shape,
                    "parallelism": f"replicas x{world}"},
         "grid": grid,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
