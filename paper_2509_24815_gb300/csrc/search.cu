@@ -18,104 +18,30 @@
 //      r < theta / hf); r is non-increasing and theta non-decreasing along
 //      the order, so the first skipped block ends the list.
 //  H5  forward rows: groups of G lanes score one document each; a row is a
-//      record of 8-entry chunks (16 B of terms then 32 B of values per chunk),
-//      read with 16-byte vector loads.  Each document is scored at most once
-//      per query (a bounded shared-memory hash set; on overflow a document may
-//      be scored again, which changes no result).
+//      record of 8-entry chunks read with 16-byte vector loads.  At the start
+//      of a wave every row of the wave is prefetched into L2 with one TMA bulk
+//      prefetch per document, and the member lists of the next wave's blocks
+//      too, so the groups' sequential row reads hit L2.  Each document is
+//      scored at most once per query (a global bitmap per persistent CTA, or
+//      a bounded shared-memory hash set).
 //  H6  top-k by (score desc, id asc): candidates that beat the k-th score are
 //      collected per wave and merged by rank.
 //  H7  kappa-NN expansion of the top-k after the lists (S fixed first).
 //
 // Waves: with wave = 1 every block is evaluated before the next skip test,
 // which is exactly the sequential order of the algorithm (the final heap
-// after a block does not depend on the order of its documents).
+// after a block does not depend on the order of its documents).  With wave =
+// W the next W blocks that pass the test against the threshold at the wave's
+// start are evaluated together (batch-synchronous).
 #include <algorithm>
 
-#include "search_impl.h"
+#include "search_common.cuh"
 
 namespace seismic {
 
 namespace {
 
-__device__ __forceinline__ uint32_t f2ord(float f) {
-  uint32_t u = __float_as_uint(f);
-  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-}
-__device__ __forceinline__ float ord2f(uint32_t o) {
-  uint32_t u = (o & 0x80000000u) ? (o & 0x7FFFFFFFu) : ~o;
-  return __uint_as_float(u);
-}
-
-__device__ __forceinline__ bool better(float s1, uint32_t i1, float s2, uint32_t i2) {
-  return s1 > s2 || (s1 == s2 && i1 < i2);
-}
-
-__device__ __forceinline__ float qlookup(const uint32_t *__restrict__ qbits, const uint16_t *__restrict__ qrank,
-                                         const float *__restrict__ qval, uint32_t t) {
-  const uint32_t w = qbits[t >> 5];
-  const uint32_t bit = 1u << (t & 31);
-  if (!(w & bit)) return 0.0f;
-  return qval[qrank[t >> 5] + __popc(w & (bit - 1u))];
-}
-
-// 16-byte read-only loads that do not allocate in L1: rows are touched once
-// per query, reuse across queries happens in L2.
-__device__ __forceinline__ uint4 ldg_na(const void *p) {
-  uint4 r;
-  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-               : "l"(p));
-  return r;
-}
-
-template <int G>
-__device__ __forceinline__ float doc_dot(const uint8_t *__restrict__ fwd, const uint32_t *__restrict__ cptr,
-                                         uint32_t d, int gl, uint32_t gmask, const uint32_t *__restrict__ qbits,
-                                         const uint16_t *__restrict__ qrank, const float *__restrict__ qval) {
-  const uint32_t c0 = __ldg(cptr + d), nch = __ldg(cptr + d + 1) - c0;
-  const uint8_t *rec = fwd + (size_t)c0 * 48;
-  const uint8_t *vrec = rec + 16 * (size_t)nch;
-  float acc = 0.0f;
-  uint32_t c = gl;
-#pragma unroll 1
-  for (; c + G < nch; c += 2 * G) {  // two chunks in flight per lane
-    uint4 t0 = ldg_na(rec + 16 * (size_t)c);
-    uint4 a0 = ldg_na(vrec + 32 * (size_t)c);
-    uint4 b0 = ldg_na(vrec + 32 * (size_t)c + 16);
-    uint4 t1 = ldg_na(rec + 16 * (size_t)(c + G));
-    uint4 a1 = ldg_na(vrec + 32 * (size_t)(c + G));
-    uint4 b1 = ldg_na(vrec + 32 * (size_t)(c + G) + 16);
-    const uint32_t tw0[4] = {t0.x, t0.y, t0.z, t0.w};
-    const uint32_t va0[8] = {a0.x, a0.y, a0.z, a0.w, b0.x, b0.y, b0.z, b0.w};
-    const uint32_t tw1[4] = {t1.x, t1.y, t1.z, t1.w};
-    const uint32_t va1[8] = {a1.x, a1.y, a1.z, a1.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-    for (int e = 0; e < 4; e++) {
-      acc = fmaf(qlookup(qbits, qrank, qval, tw0[e] & 0xFFFFu), __uint_as_float(va0[2 * e]), acc);
-      acc = fmaf(qlookup(qbits, qrank, qval, tw0[e] >> 16), __uint_as_float(va0[2 * e + 1]), acc);
-    }
-#pragma unroll
-    for (int e = 0; e < 4; e++) {
-      acc = fmaf(qlookup(qbits, qrank, qval, tw1[e] & 0xFFFFu), __uint_as_float(va1[2 * e]), acc);
-      acc = fmaf(qlookup(qbits, qrank, qval, tw1[e] >> 16), __uint_as_float(va1[2 * e + 1]), acc);
-    }
-  }
-  if (c < nch) {
-    uint4 t0 = ldg_na(rec + 16 * (size_t)c);
-    uint4 a0 = ldg_na(vrec + 32 * (size_t)c);
-    uint4 b0 = ldg_na(vrec + 32 * (size_t)c + 16);
-    const uint32_t tw0[4] = {t0.x, t0.y, t0.z, t0.w};
-    const uint32_t va0[8] = {a0.x, a0.y, a0.z, a0.w, b0.x, b0.y, b0.z, b0.w};
-#pragma unroll
-    for (int e = 0; e < 4; e++) {
-      acc = fmaf(qlookup(qbits, qrank, qval, tw0[e] & 0xFFFFu), __uint_as_float(va0[2 * e]), acc);
-      acc = fmaf(qlookup(qbits, qrank, qval, tw0[e] >> 16), __uint_as_float(va0[2 * e + 1]), acc);
-    }
-  }
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(gmask, acc, o, G);
-  return acc;
-}
+using namespace dev;
 
 // Insert d into the per-query seen set; true when d was not there before
 // (or the set is too crowded to tell, in which case d is scored again).
@@ -183,6 +109,7 @@ struct Smem {
   float *tk_s, *tmp_s, *cand_s;
   uint32_t *tk_id, *tmp_id, *cand_id;
   uint8_t *cand_ok;
+  uint32_t *woff, *wstart;  // the current wave's blocks
 };
 
 struct Shared {
@@ -241,9 +168,9 @@ __device__ void merge_candidates(const SearchArgs &a, Smem &s, Shared &sh) {
   __syncthreads();
 }
 
-// Scores up to CAND documents drawn from a source functor, then merges.
+// Scores up to CAND documents of a source, then merges the candidates.
 template <int G, int NT, class Src>
-__device__ void eval_wave(const SearchArgs &a, Smem &s, Shared &sh, uint32_t n, Src src, int knn_stage) {
+__device__ void eval_wave(const SearchArgs &a, Smem &s, Shared &sh, uint32_t n, const Src &src, int knn_stage) {
   constexpr int NG = NT / G;
   const int tid = threadIdx.x, grp = tid / G, gl = tid % G;
   const uint32_t lane = tid & 31;
@@ -251,9 +178,16 @@ __device__ void eval_wave(const SearchArgs &a, Smem &s, Shared &sh, uint32_t n, 
   const bool full = sh.count == a.k;
   const float th = full ? s.tk_s[a.k - 1] : -INFINITY;
   const uint32_t thid = full ? s.tk_id[a.k - 1] : 0u;
+  if (a.prefetch && n > (uint32_t)NG) {  // every row of the wave into L2, one bulk prefetch each
+    for (uint32_t i = tid; i < n; i += NT) {
+      const uint32_t d = src.id(i);
+      if (d != SEISMIC_NONE_ID) prefetch_row(a.fwd_data, src.row(i, d));
+    }
+  }
   for (uint32_t i = grp; i < n; i += NG) {
-    const uint32_t d = src(i);
+    const uint32_t d = src.id(i);
     if (d == SEISMIC_NONE_ID) continue;
+    const unsigned long long row = src.row(i, d);
     uint32_t fresh = 0;
     if (gl == 0) {
       if (s.seen) {
@@ -265,7 +199,8 @@ __device__ void eval_wave(const SearchArgs &a, Smem &s, Shared &sh, uint32_t n, 
     }
     fresh = __shfl_sync(gmask, fresh, 0, G);
     if (!fresh) continue;
-    const float p = doc_dot<G>(a.fwd_data, a.fwd_cptr, d, gl, gmask, s.qbits, s.qrank, s.qval);
+    const float p = row_dot<G>(a.fwd_data, (uint32_t)row, (uint32_t)(row >> 32), gl, gmask, s.qbits, s.qrank,
+                               s.qval);
     if (gl == 0) {
       if (a.stats) {
         atomicAdd(&sh.st[knn_stage ? SEISMIC_ST_KNN_DOCS : SEISMIC_ST_DOCS], 1ull);
@@ -323,6 +258,8 @@ __global__ void __launch_bounds__(NW * 32) k_search(const SearchArgs a) {
   s.cand_s = reinterpret_cast<float *>(sm + a.off_cand_s);
   s.cand_id = reinterpret_cast<uint32_t *>(sm + a.off_cand_id);
   s.cand_ok = reinterpret_cast<uint8_t *>(sm + a.off_cand_ok);
+  s.woff = reinterpret_cast<uint32_t *>(sm + a.off_wave);
+  s.wstart = s.woff + (kMaxWave + 1);
   s.seen = a.seen_bm ? a.seen_bm + (size_t)blockIdx.x * a.seen_words : nullptr;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   bool first = true;
@@ -449,8 +386,8 @@ __global__ void __launch_bounds__(NW * 32) k_search(const SearchArgs a) {
         }
         for (uint32_t c0 = d0; c0 < d1; c0 += a.CAND) {
           const uint32_t n = min(a.CAND, d1 - c0);
-          const uint32_t *src = a.bdoc + c0;
-          eval_wave<G, NT>(a, s, sh, n, [src](uint32_t i) { return __ldg(src + i); }, 0);
+          const MemberSrc src{a.bdoc + c0, a.bdoc_row + c0};
+          eval_wave<G, NT>(a, s, sh, n, src, 0);
         }
         continue;
       }
@@ -503,79 +440,65 @@ __global__ void __launch_bounds__(NW * 32) k_search(const SearchArgs a) {
       // ---- H3: order blocks by (r desc, block asc)
       bitonic_sort_u64<NT>(s.keys, P2);
       // ---- H4/H5/H6: visit blocks in order, waves of a.wave blocks
+      const uint32_t W = min(a.wave, kMaxWave);
       uint32_t bi = 0;
       while (bi < nb) {
         // skip test at the head of the wave (uniform: shared state after a barrier)
-        if (sh.count == a.k) {
-          const float theta = s.tk_s[a.k - 1];
-          const float thr = a.hf_mode == 0 ? hf * theta : theta / hf;
-          const float r = ord2f(~(uint32_t)(s.keys[bi] >> 32));
-          if (r < thr) {
-            if (a.stats && tid == 0) sh.st[SEISMIC_ST_BLOCKS_SKIPPED] += nb - bi;
-            break;
-          }
+        const bool fullk = sh.count == a.k;
+        const float theta = fullk ? s.tk_s[a.k - 1] : -INFINITY;
+        const float thr = a.hf_mode == 0 ? hf * theta : theta / hf;
+        if (fullk && ord2f(~(uint32_t)(s.keys[bi] >> 32)) < thr) {
+          if (a.stats && tid == 0) sh.st[SEISMIC_ST_BLOCKS_SKIPPED] += nb - bi;
+          break;
         }
-        if (a.wave <= 1) {
+        // the wave: the next blocks that pass the test against theta now, up to
+        // W blocks and CAND documents (a larger block goes alone, in pieces)
+        uint32_t be = bi, ndocs = 0;
+        while (be < nb && be - bi < W) {
+          const uint32_t b = (uint32_t)(s.keys[be] & 0xFFFFFFFFu);
+          if (be > bi && fullk && ord2f(~(uint32_t)(s.keys[be] >> 32)) < thr) break;
+          const uint32_t nd = a.bdoc_ptr[g0 + b + 1] - a.bdoc_ptr[g0 + b];
+          if (be > bi && ndocs + nd > a.CAND) break;
+          ndocs += nd;
+          be++;
+        }
+        if (a.prefetch && tid < W && be + tid < nb) {  // member lists of the next wave's blocks
+          const uint32_t b = (uint32_t)(s.keys[be + tid] & 0xFFFFFFFFu);
+          const uint32_t e0 = __ldg(a.bdoc_ptr + g0 + b), e1 = __ldg(a.bdoc_ptr + g0 + b + 1);
+          prefetch_l2(a.bdoc + e0, 4 * (e1 - e0));
+          prefetch_l2(a.bdoc_row + e0, 8 * (e1 - e0));
+        }
+        if (a.stats && tid == 0) {
+          sh.st[SEISMIC_ST_BLOCKS_EVALUATED] += be - bi;
+          sh.st[SEISMIC_ST_BLOCK_DOCS] += ndocs;
+        }
+        if (be - bi == 1) {
           const uint32_t b = (uint32_t)(s.keys[bi] & 0xFFFFFFFFu);
           const uint32_t d0 = a.bdoc_ptr[g0 + b], d1 = a.bdoc_ptr[g0 + b + 1];
-          if (a.stats && tid == 0) {
-            sh.st[SEISMIC_ST_BLOCKS_EVALUATED]++;
-            sh.st[SEISMIC_ST_BLOCK_DOCS] += d1 - d0;
-          }
           for (uint32_t c0 = d0; c0 < d1; c0 += a.CAND) {
-            const uint32_t n = min(a.CAND, d1 - c0);
-            const uint32_t *src = a.bdoc + c0;
-            eval_wave<G, NT>(a, s, sh, n, [src](uint32_t i) { return __ldg(src + i); }, 0);
+            const MemberSrc src{a.bdoc + c0, a.bdoc_row + c0};
+            eval_wave<G, NT>(a, s, sh, min(a.CAND, d1 - c0), src, 0);
           }
-          bi++;
         } else {
-          // a wave: the next blocks whose score passes the test against the
-          // threshold at the wave's start, up to a.wave blocks / CAND documents
-          uint32_t be = bi, ndocs = 0;
-          const bool fullk = sh.count == a.k;
-          const float theta = fullk ? s.tk_s[a.k - 1] : -INFINITY;
-          const float thr = a.hf_mode == 0 ? hf * theta : theta / hf;
-          while (be < nb && be - bi < a.wave) {
-            const uint32_t b = (uint32_t)(s.keys[be] & 0xFFFFFFFFu);
-            const float r = ord2f(~(uint32_t)(s.keys[be] >> 32));
-            if (fullk && r < thr) break;
-            const uint32_t nd = a.bdoc_ptr[g0 + b + 1] - a.bdoc_ptr[g0 + b];
-            if (be > bi && ndocs + nd > a.CAND) break;
-            ndocs += nd;
-            be++;
+          if (tid < be - bi) {
+            const uint32_t b = (uint32_t)(s.keys[bi + tid] & 0xFFFFFFFFu);
+            s.wstart[tid] = a.bdoc_ptr[g0 + b];
           }
-          if (ndocs > a.CAND) {  // one oversized block: evaluate it alone, in pieces
-            const uint32_t b = (uint32_t)(s.keys[bi] & 0xFFFFFFFFu);
-            const uint32_t d0 = a.bdoc_ptr[g0 + b], d1 = a.bdoc_ptr[g0 + b + 1];
-            for (uint32_t c0 = d0; c0 < d1; c0 += a.CAND) {
-              const uint32_t n = min(a.CAND, d1 - c0);
-              const uint32_t *src = a.bdoc + c0;
-              eval_wave<G, NT>(a, s, sh, n, [src](uint32_t i) { return __ldg(src + i); }, 0);
+          __syncthreads();
+          if (tid == 0) {
+            uint32_t acc = 0;
+            for (uint32_t w = 0; w < be - bi; w++) {
+              s.woff[w] = acc;
+              const uint32_t b = (uint32_t)(s.keys[bi + w] & 0xFFFFFFFFu);
+              acc += a.bdoc_ptr[g0 + b + 1] - s.wstart[w];
             }
-          } else {
-            // per-document source over the wave's blocks (walk the block list)
-            const unsigned long long *keys = s.keys;
-            const uint32_t *bdp = a.bdoc_ptr + g0;
-            const uint32_t *bd = a.bdoc;
-            const uint32_t b0 = bi, nbw = be - bi;
-            eval_wave<G, NT>(a, s, sh, ndocs,
-                             [keys, bdp, bd, b0, nbw](uint32_t i) {
-                               for (uint32_t w = 0; w < nbw; w++) {
-                                 const uint32_t b = (uint32_t)(keys[b0 + w] & 0xFFFFFFFFu);
-                                 const uint32_t lo = __ldg(bdp + b), n = __ldg(bdp + b + 1) - lo;
-                                 if (i < n) return __ldg(bd + lo + i);
-                                 i -= n;
-                               }
-                               return SEISMIC_NONE_ID;
-                             },
-                             0);
+            s.woff[be - bi] = acc;
           }
-          if (a.stats && tid == 0) {
-            sh.st[SEISMIC_ST_BLOCKS_EVALUATED] += be - bi;
-            sh.st[SEISMIC_ST_BLOCK_DOCS] += ndocs;
-          }
-          bi = be;
+          __syncthreads();
+          const WaveSrc src{s.woff, s.wstart, be - bi, a.bdoc, a.bdoc_row};
+          eval_wave<G, NT>(a, s, sh, ndocs, src, 0);
         }
+        bi = be;
       }
       __syncthreads();
     }
@@ -583,23 +506,20 @@ __global__ void __launch_bounds__(NW * 32) k_search(const SearchArgs a) {
     // ---------------------------------------------------------- H7: kappa-NN expansion
     if (a.use_knn && a.kappa > 0 && sh.count > 0) {
       const uint32_t ns = sh.count;
-      for (uint32_t i = tid; i < ns; i += NT) s.tmp_id[i] = s.tk_id[i];  // S, fixed before expanding
-      __syncthreads();
-      // tmp_id is rewritten by merges: keep S in the candidate-id area's tail? use clo (>= k entries)
-      for (uint32_t i = tid; i < ns; i += NT) s.clo[i] = s.tmp_id[i];
+      for (uint32_t i = tid; i < ns; i += NT) s.clo[i] = s.tk_id[i];  // S, fixed before expanding
       __syncthreads();
       const uint32_t total = ns * a.kappa;
-      const uint32_t *S = s.clo;
-      const uint32_t *knn = a.knn;
-      const uint32_t kappa = a.kappa;
       for (uint32_t c0 = 0; c0 < total; c0 += a.CAND) {
         const uint32_t n = min(a.CAND, total - c0);
-        eval_wave<G, NT>(a, s, sh, n,
-                         [S, knn, kappa, c0](uint32_t i) {
-                           const uint32_t x = c0 + i;
-                           return __ldg(knn + (size_t)S[x / kappa] * kappa + (x % kappa));
-                         },
-                         1);
+        const GraphSrc src{s.clo, a.knn + (size_t)0, a.fwd_cptr, a.kappa};
+        // positions c0 .. c0 + n of the neighbour list of S
+        struct Shifted {
+          GraphSrc g;
+          uint32_t c0;
+          __device__ uint32_t id(uint32_t i) const { return g.id(c0 + i); }
+          __device__ unsigned long long row(uint32_t i, uint32_t d) const { return g.row(c0 + i, d); }
+        } sh_src{src, c0};
+        eval_wave<G, NT>(a, s, sh, n, sh_src, 1);
       }
     }
 
@@ -664,6 +584,7 @@ size_t search_layout(SearchArgs &a, uint32_t nw) {
   a.off_cand_s = take(a.CAND * 4);
   a.off_cand_id = take(a.CAND * 4);
   a.off_cand_ok = take(a.CAND);
+  a.off_wave = take(2 * (kMaxWave + 1) * 4);
   return o;
 }
 

@@ -55,9 +55,10 @@ struct SearchArgs {
   // shared-memory layout
   uint32_t W, QN, BMAX, BPOW2, HS, CAND;
   uint32_t off_qbits, off_qrank, off_qval, off_qterm, off_cut, off_aq, off_part, off_keys, off_clo, off_chi,
-      off_hash, off_tk_s, off_tk_id, off_tmp_s, off_tmp_id, off_cand_s, off_cand_id, off_cand_ok;
+      off_hash, off_tk_s, off_tk_id, off_tmp_s, off_tmp_id, off_cand_s, off_cand_id, off_cand_ok, off_wave;
 };
 
+constexpr uint32_t kMaxWave = 64;  // blocks per wave (CTA kernel)
 size_t search_layout(SearchArgs &a, uint32_t nw);
 int launch_search(const SearchArgs &a, uint32_t group, uint32_t nw, size_t smem, uint32_t grid, cudaStream_t st);
 int search_occupancy(uint32_t group, uint32_t nw, size_t smem, int *blocks);
