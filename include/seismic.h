@@ -105,8 +105,11 @@ typedef struct {
                             query; 1: one CTA per query (any k, any wave); 2: one warp per
                             query (persistent, cta_warps independent warps per CTA: 1/2/4,
                             0 = 4).  Both keep the algorithm's sequential order at wave 1 */
-  int32_t no_prefetch;   /* warp shape: 1 turns off the L2 bulk prefetch of the next blocks'
-                            member lists and rows (a speed knob; results are the same) */
+  int32_t no_prefetch;   /* 1 turns off the L2 bulk prefetch of upcoming member lists and rows
+                            (a speed knob; results are the same) */
+  uint32_t order;        /* persistent launches: 0 (default) runs queries grouped by their
+                            largest term, so queries reading the same lists share L2; 1 runs
+                            them in input order.  Results do not depend on it */
 } seismic_search_params;
 
 /* Per-query work counters written by seismic_search when `stats` is non-NULL:

@@ -54,6 +54,47 @@ __global__ void k_fwd_to_csr(const uint32_t *cptr, const uint8_t *data, uint64_t
   }
 }
 
+// Work-queue order of a persistent search: queries sorted by their largest
+// term (the first list they traverse), so queries that read the same lists,
+// blocks and rows run at the same time and share them through L2.  Results do
+// not depend on the order.
+__global__ void k_order_keys(const uint64_t *ip, const uint16_t *t, const float *v, uint32_t nq,
+                             unsigned long long *keys) {
+  const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  float bv = -INFINITY;
+  uint32_t bt = 0xFFFFu;
+  for (uint64_t p = ip[q]; p < ip[q + 1]; p++) {
+    const float x = v[p];
+    const uint32_t tt = t[p];
+    if (x != 0.0f && (x > bv || (x == bv && tt < bt))) { bv = x; bt = tt; }
+  }
+  keys[q] = ((unsigned long long)bt << 32) | q;
+}
+
+constexpr uint32_t kOrderChunk = 8192;
+
+__global__ void __launch_bounds__(1024) k_order_sort(const unsigned long long *keys, uint32_t nq, uint32_t *perm) {
+  extern __shared__ unsigned long long sk[];
+  const uint32_t c0 = blockIdx.x * kOrderChunk, n = min(kOrderChunk, nq - c0);
+  uint32_t P2 = 1;
+  while (P2 < n) P2 <<= 1;
+  for (uint32_t i = threadIdx.x; i < P2; i += blockDim.x) sk[i] = i < n ? keys[c0 + i] : ~0ull;
+  __syncthreads();
+  for (uint32_t k2 = 2; k2 <= P2; k2 <<= 1)
+    for (uint32_t j = k2 >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < P2; i += blockDim.x) {
+        const uint32_t ixj = i ^ j;
+        if (ixj > i) {
+          const unsigned long long x = sk[i], y = sk[ixj];
+          if ((x > y) == ((i & k2) == 0)) { sk[i] = y; sk[ixj] = x; }
+        }
+      }
+      __syncthreads();
+    }
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) perm[c0 + i] = (uint32_t)(sk[i] & 0xFFFFFFFFu);
+}
+
 int sm_count(int dev) {
   int sms = 1;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -223,6 +264,22 @@ int search_impl(seismic_index *ix, const seismic_csr *queries, const seismic_sea
   const uint32_t nw = p->cta_warps ? p->cta_warps : 8, group = p->group ? p->group : 8;
   a.sum_absmax = ix->sum_absmax;
   a.prefetch = p->no_prefetch ? 0u : 256u;
+  const bool warp_shape0 = p->shape == 2 || (p->shape == 0 && k <= 128 && a.wave <= 1);
+  if (p->order == 0 && nq > 1 && (a.persistent || warp_shape0)) {
+    if ((rc = ix->ws_perm.ensure((size_t)nq * 12))) return rc;
+    unsigned long long *keys = ix->ws_perm.as<unsigned long long>();
+    uint32_t *perm = reinterpret_cast<uint32_t *>(keys + nq);
+    k_order_keys<<<(nq + 255) / 256, 256, 0, st>>>(q.ip, q.t, q.v, nq, keys);
+    SZ_CUDA(cudaGetLastError());
+    static bool attr = false;
+    if (!attr) {
+      SZ_CUDA(cudaFuncSetAttribute(k_order_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, kOrderChunk * 8));
+      attr = true;
+    }
+    k_order_sort<<<(nq + kOrderChunk - 1) / kOrderChunk, 1024, kOrderChunk * 8, st>>>(keys, nq, perm);
+    SZ_CUDA(cudaGetLastError());
+    a.perm = perm;
+  }
   // shape: one warp per query (default when k <= 128 and wave = 1) or one CTA per query
   const bool warp_shape = p->shape == 2 || (p->shape == 0 && k <= 128 && a.wave <= 1);
   if (warp_shape) {

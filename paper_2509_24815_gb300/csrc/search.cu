@@ -266,7 +266,10 @@ __global__ void __launch_bounds__(NW * 32) k_search(const SearchArgs a) {
 
   for (;;) {
     if (tid == 0) {
-      if (a.persistent) sh.q = atomicAdd(a.queue, 1u);
+      if (a.persistent) {
+        const uint32_t slot = atomicAdd(a.queue, 1u);
+        sh.q = (a.perm && slot < a.nq) ? a.perm[slot] : slot;
+      }
       else sh.q = first ? blockIdx.x : a.nq;
     }
     first = false;

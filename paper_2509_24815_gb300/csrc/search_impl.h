@@ -52,6 +52,7 @@ struct SearchArgs {
   uint32_t warp_bytes;
   float sum_absmax;
   uint32_t prefetch;  // rows of the next block prefetched into L2 (at most this many; 0 = off)
+  const uint32_t *perm;  // persistent launches pull queries in this order (NULL: 0, 1, 2, ...)
   // shared-memory layout
   uint32_t W, QN, BMAX, BPOW2, HS, CAND;
   uint32_t off_qbits, off_qrank, off_qval, off_qterm, off_cut, off_aq, off_part, off_keys, off_clo, off_chi,

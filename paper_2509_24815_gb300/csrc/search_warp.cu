@@ -180,7 +180,10 @@ __global__ void __launch_bounds__(128, 5) k_search_warp(const SearchArgs a) {
 
   for (;;) {
     uint32_t q = 0;
-    if (lane == 0) q = atomicAdd(a.queue, 1u);
+    if (lane == 0) {
+      const uint32_t slot = atomicAdd(a.queue, 1u);
+      q = (a.perm && slot < a.nq) ? a.perm[slot] : slot;
+    }
     q = __shfl_sync(0xffffffffu, q, 0);
     if (q >= a.nq) break;
     WarpCounters st;

@@ -163,6 +163,7 @@ struct seismic_index {
   seismic::DevBuf ws_feat;
   seismic::DevBuf ws_exact;  // exact-search accumulators
   seismic::DevBuf ws_seen;   // per-CTA seen bitmaps of persistent searches
+  seismic::DevBuf ws_perm;   // work-queue order keys and permutation
 };
 
 namespace seismic {
