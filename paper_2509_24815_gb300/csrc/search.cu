@@ -184,23 +184,34 @@ __device__ void eval_wave(const SearchArgs &a, Smem &s, Shared &sh, uint32_t n, 
       if (d != SEISMIC_NONE_ID) prefetch_row(a.fwd_data, src.row(i, d));
     }
   }
+  // Software pipeline per lane group: the next document's (id, row) are loaded
+  // while the current one is scored, and the seen-bitmap test is issued with
+  // the row's loads and read after the dot (a seen document's score is dropped).
+  uint32_t dn = SEISMIC_NONE_ID;
+  unsigned long long rn = 0ull;
+  if ((uint32_t)grp < n) {
+    dn = src.id(grp);
+    rn = src.row(grp, dn);
+  }
   for (uint32_t i = grp; i < n; i += NG) {
-    const uint32_t d = src.id(i);
-    if (d == SEISMIC_NONE_ID) continue;
-    const unsigned long long row = src.row(i, d);
-    uint32_t fresh = 0;
-    if (gl == 0) {
-      if (s.seen) {
-        const uint32_t bit = 1u << (d & 31);
-        fresh = (atomicOr(s.seen + (d >> 5), bit) & bit) ? 0u : 1u;
-      } else {
-        fresh = seen_insert(s.hash, a.HS - 1u, d, &sh.hash_full) ? 1u : 0u;
-      }
+    const uint32_t d = dn;
+    const unsigned long long row = rn;
+    if (i + NG < n) {
+      dn = src.id(i + NG);
+      rn = src.row(i + NG, dn);
     }
-    fresh = __shfl_sync(gmask, fresh, 0, G);
-    if (!fresh) continue;
+    if (d == SEISMIC_NONE_ID) continue;
+    uint32_t old = 0u, fresh = 0u;
+    const uint32_t bit = 1u << (d & 31);
+    if (gl == 0) {
+      if (s.seen) old = atomicOr(s.seen + (d >> 5), bit);
+      else fresh = seen_insert(s.hash, a.HS - 1u, d, &sh.hash_full) ? 1u : 0u;
+    }
     const float p = row_dot<G>(a.fwd_data, (uint32_t)row, (uint32_t)(row >> 32), gl, gmask, s.qbits, s.qrank,
                                s.qval);
+    if (s.seen) fresh = (old & bit) ? 0u : 1u;
+    fresh = __shfl_sync(gmask, fresh, 0, G);
+    if (!fresh) continue;
     if (gl == 0) {
       if (a.stats) {
         atomicAdd(&sh.st[knn_stage ? SEISMIC_ST_KNN_DOCS : SEISMIC_ST_DOCS], 1ull);
@@ -235,7 +246,7 @@ __device__ void bitonic_sort_u64(unsigned long long *keys, uint32_t P2) {
 }
 
 template <int G, int NW>
-__global__ void __launch_bounds__(NW * 32) k_search(const SearchArgs a) {
+__global__ void __launch_bounds__(NW * 32, 1280 / (NW * 32)) k_search(const SearchArgs a) {
   constexpr int NT = NW * 32;
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ Shared sh;

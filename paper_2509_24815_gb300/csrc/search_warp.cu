@@ -116,13 +116,24 @@ __device__ void eval_docs(const SearchArgs &a, const WarpSmem &s, uint32_t *seen
   constexpr int NG = 32 / G;
   const int grp = lane / G, gl = lane % G;
   const uint32_t gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+  // the next round's (id, row) are loaded while this round is scored
+  uint32_t dn = SEISMIC_NONE_ID;
+  unsigned long long rn = 0ull;
+  if ((uint32_t)grp < n) {
+    dn = src.id(grp);
+    rn = src.row(grp, dn);
+  }
   for (uint32_t base = 0; base < n; base += NG) {
     const uint32_t i = base + grp;
     uint32_t d = SEISMIC_NONE_ID, old = 0u, bit = 0u;
     unsigned long long row = 0ull;
     if (i < n) {
-      d = src.id(i);
-      row = src.row(i, d);  // for block members this load does not wait for d
+      d = dn;
+      row = rn;
+      if (i + NG < n) {
+        dn = src.id(i + NG);
+        rn = src.row(i + NG, dn);
+      }
       if (d != SEISMIC_NONE_ID) {
         bit = 1u << (d & 31);
         if (gl == 0) old = atomicOr(seen + (d >> 5), bit);
