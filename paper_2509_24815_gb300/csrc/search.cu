@@ -246,7 +246,7 @@ __device__ void bitonic_sort_u64(unsigned long long *keys, uint32_t P2) {
 }
 
 template <int G, int NW>
-__global__ void __launch_bounds__(NW * 32, 1024 / (NW * 32)) k_search(const SearchArgs a) {
+__global__ void __launch_bounds__(NW * 32, 1280 / (NW * 32)) k_search(const SearchArgs a) {
   constexpr int NT = NW * 32;
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ Shared sh;
