@@ -245,6 +245,35 @@ int seismic_mlp_train_step(float *weights, float *grads, float *adam_m, float *a
                            const float *features, const float *targets, uint64_t n, float lr,
                            uint32_t step, float *loss_out, void *stream);
 
+/* Query processing that allocates no memory (this entry point has no
+ * counterpart in the paper; it is for callers that cannot allocate device
+ * memory while they serve queries: a process whose memory pool is fixed at
+ * start-up, or one that keeps cudaMalloc's device synchronisation off its
+ * latency path).  It runs the same CTA-per-query persistent kernel as
+ * seismic_search with the same results, and calls no cudaMalloc, cudaFree or
+ * allocating library routine.
+ *   - queries, ids_out and scores_out must be device buffers; params must set
+ *     max_query_nnz; stats, learned parameters and work-queue ordering are not
+ *     available here (queries run in input order; results are the same).
+ *   - Working memory is one fixed 32 MiB device array inside the library,
+ *     held by every GPU that loads it until the process exits: a 256-byte
+ *     header (queue counter, error word, cleared on `stream` at each call)
+ *     and one seen bitmap of ceil(n_docs / 32) words per persistent CTA.  The
+ *     number of CTAs is capped by what fits; an index whose single bitmap does
+ *     not fit (more than about 268 million documents) gets SEISMIC_EBUDGET.
+ *   - The first call on a device looks the array's device address up
+ *     (cudaGetSymbolAddress, with that device current) and caches it: make
+ *     that first call before any stream capture.
+ *   - Every call shares the array and enqueues its work on `stream` without
+ *     waiting: calls that overlap on the GPU (other streams, other threads,
+ *     other indexes on the same device) race on it.  Serialise them.
+ *   - A malformed device query (more nonzeros than max_query_nnz) yields a
+ *     padded row, as in seismic_search's device path.
+ * Errors: EINVAL (arguments), EBUDGET (collection too large for the fixed
+ * array), ECUDA. */
+int seismic_search_noalloc(seismic_index *index, const seismic_csr *queries, const seismic_search_params *params,
+                           uint32_t *ids_out, float *scores_out, void *stream);
+
 void seismic_free(seismic_index *index);
 const char *seismic_last_error(void);
 const char *seismic_version(void);

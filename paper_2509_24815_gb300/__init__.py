@@ -86,6 +86,7 @@ _SIGS = {
     "seismic_query_features": ([_vp, _P(_CSR), _vp, _i32, _vp], ctypes.c_int),
     "seismic_mlp_forward": ([_vp, _vp, _u64, _vp, _vp], ctypes.c_int),
     "seismic_mlp_train_step": ([_vp, _vp, _vp, _vp, _vp, _vp, _u64, _f32, _u32, _vp, _vp], ctypes.c_int),
+    "seismic_search_noalloc": ([_vp, _P(_CSR), _P(SearchParams), _vp, _vp, _vp], ctypes.c_int),
     "seismic_free": ([_vp], None),
     "seismic_last_error": ([], ctypes.c_char_p),
     "seismic_version": ([], ctypes.c_char_p),
@@ -322,6 +323,18 @@ def seismic_mlp_train_step(weights, grads, adam_m, adam_v, features, targets, lr
     _check(_lib.seismic_mlp_train_step(weights.data_ptr(), grads.data_ptr(), adam_m.data_ptr(), adam_v.data_ptr(),
                                        features.data_ptr(), targets.data_ptr(), features.shape[0], float(lr),
                                        int(step), loss_out.data_ptr(), _stream_ptr(stream)))
+
+
+def seismic_search_noalloc(index: Index, queries: DeviceCSR, params: SearchParams, ids_out, scores_out,
+                           stream=None):
+    """Search with no memory allocation (device queries and outputs, torch CUDA
+    tensors); work memory is the library's fixed device array.  Enqueued on
+    ``stream`` without waiting; calls that overlap on the GPU race."""
+    if not params.max_query_nnz:
+        params.max_query_nnz = queries.max_row_nnz
+    s, keep = _csr_struct(queries)
+    _check(_lib.seismic_search_noalloc(index.handle, ctypes.byref(s), ctypes.byref(params), ids_out.data_ptr(),
+                                       scores_out.data_ptr(), _stream_ptr(stream)))
 
 
 def seismic_free(index: Index):
