@@ -38,12 +38,12 @@ WORKLOADS = {
     "c2": dict(desc="Seismic 1M docs, vocab 30522, lambda=6000, beta=400, alpha=0.4, u8 summaries, "
                     "10k queries (uniform nnz 10-150), k=10, grid cut {5,10,20} x hf {0.6..0.9}",
                n_docs=1_000_000, n_q=10_000, uneven=True, lam=6000, beta=400, alpha=0.4, quant=True,
-               cuts=(5, 10, 20), hfs=(0.6, 0.7, 0.8, 0.9), kappa=0, cpu_sample=200),
+               cuts=(5, 10, 20), hfs=(0.6, 0.7, 0.8, 0.9), kappa=0, cpu_sample=200, n_train=20_000),
     # the c2 shape at 300k documents and 2k queries: small enough for multi-pass ncu captures
     "c2s": dict(desc="Seismic 300k docs, vocab 30522, lambda=6000, beta=400, alpha=0.4, u8 summaries, "
                      "2k queries (uniform nnz 10-150), k=10, cut=5, heap_factor=0.9", n_docs=300_000, n_q=2000,
                 uneven=True, lam=6000, beta=400, alpha=0.4, quant=True, cuts=(5,), hfs=(0.9,), kappa=0,
-                cpu_sample=100),
+                cpu_sample=100, n_train=4000),
     "c3": dict(desc="Seismic 8.8M docs, vocab 30522, lambda=6000, beta=400, alpha=0.4, u8 summaries, kappa=10, "
                     "10k queries (uniform nnz 10-150), k=10", n_docs=8_800_000, n_q=10_000, uneven=True, lam=6000,
                beta=400, alpha=0.4, quant=True, cuts=(5, 10, 20), hfs=(0.6, 0.7, 0.8, 0.9), kappa=10,
@@ -150,6 +150,46 @@ def cpu_baseline(w, docs, queries, cut, hf, steps=1):
                       f"thread; lists built untimed", "times_s": times}
 
 
+def learned_eval(args, w, sz, ix, dq, gt_sc, stream, time_runs):
+    """Trains the per-query parameter MLP on separate synthetic training
+    queries (labels from the method's own runs), then measures the learned form
+    on the benchmark's queries against the fixed form at equal recall."""
+    import torch
+    import synth
+    from paper_2509_24815_gb300 import learn, metrics
+    t = time.time()
+    tq = synth.queries(w["n_train"], seed=0, uneven=w["uneven"], stream=synth.TRAIN_STREAM)
+    dtq = sz.DeviceCSR.from_host(tq)
+    base = dict(shape=args.shape, wave=args.wave, persistent=bool(args.persistent))
+    res = learn.fit(ix, dtq, tq, k=K, target=args.learn_target, quantized=w["quant"], steps=3000, base_params=base)
+    t_fit = time.time() - t
+    log(f"learned: labels + training on {tq.n_rows} queries in {t_fit:.1f}s, final loss {res['trace'][-1][1]:.4f}")
+
+    def measure(**kw):
+        p = sz.search_params(k=K, max_query_nnz=dq.max_row_nnz, **base, **kw)
+        ids, sc = sz.seismic_search(ix, dq, p)
+        torch.cuda.synchronize()
+        rec = float(metrics.recall_at_k(ids.cpu().numpy().view(np.uint32), sc.cpu().numpy(), gt_sc, K).mean())
+        for _ in range(2):
+            sz.seismic_search(ix, dq, p, stream=stream)
+        ms = float(np.median(time_runs(p, max(3, args.steps))))
+        return dict(recall=rec, ms=ms, qps=dq.n_rows / ms * 1e3)
+
+    lr = measure(cut=10, heap_factor=0.8, learned=True)
+    fine = []
+    for cut in (3, 4, 5, 6, 8, 10):
+        for hf in (0.6, 0.7, 0.8, 0.9, 1.0):
+            fine.append(dict(cut=cut, heap_factor=hf, **measure(cut=cut, heap_factor=hf)))
+    at = [f for f in fine if f["recall"] >= lr["recall"] - 1e-9]
+    ref = max(at, key=lambda f: f["qps"]) if at else max(fine, key=lambda f: f["recall"])
+    log(f"learned: recall {lr['recall']:.4f} at {lr['qps']:,.0f} q/s; best fixed at >= that recall: "
+        f"cut={ref['cut']} hf={ref['heap_factor']} recall {ref['recall']:.4f} at {ref['qps']:,.0f} q/s")
+    return {"value": lr["qps"], "unit": "queries/s", "recall@10": lr["recall"], "ms_per_step": lr["ms"],
+            "fixed_at_equal_recall": ref, "qps_gain_vs_fixed": lr["qps"] / ref["qps"],
+            "train_queries": tq.n_rows, "label_target_recall": args.learn_target, "fit_seconds": t_fit,
+            "final_loss": res["trace"][-1][1], "fixed_fine_grid": fine}
+
+
 def run_reference(args, w):
     """The reference arm: the oracle timed on the host cores."""
     rank = int(os.environ.get("RANK", "0"))
@@ -181,6 +221,8 @@ def main():
     ap.add_argument("--wave", type=int, default=16)
     ap.add_argument("--persistent", type=int, default=1)
     ap.add_argument("--shape", type=int, default=1, help="1: CTA per query, 2: warp per query, 0: auto")
+    ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--learn-target", type=float, default=0.9)
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -325,6 +367,8 @@ def main():
         "index": {k: info[k] for k in ("n_docs", "nnz", "n_postings", "n_blocks", "n_summary_entries",
                                        "device_bytes")},
     }
+    if not args.no_learned and w.get("n_train"):
+        line["learned"] = learned_eval(args, w, sz, ix, dq, gt_sc, stream, time_runs)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(w, docs, queries, best["cut"], best["heap_factor"])
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}

@@ -1,0 +1,128 @@
+"""Learned per-query search parameters (not in the paper, which tunes alpha_q
+or cut and heap_factor globally, Section 5.3).
+
+Labels come from the method itself: every training query is searched at each
+(cut, heap_factor) of a grid, its recall@10 is judged against the exact top-10
+(brute force on the device), and its label is the cheapest grid point (fewest
+bytes read, from the search's work counters) whose recall reaches the target.
+The MLP (64 -> 128 -> 64 -> 2, ReLU, bf16 activations) is trained on the GPU by
+the library's own forward/backward/Adam kernels and installed in the index;
+``learned=1`` searches then run the feature and MLP kernels ahead of the
+search, with the fixed parameters as the fallback for non-finite outputs.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import (MLP_PARAMS, DeviceCSR, STATS, search_params, seismic_query_features, seismic_search,
+               seismic_search_exact, seismic_set_mlp, seismic_mlp_train_step, seismic_mlp_forward)
+from .metrics import algorithmic_bytes, recall_at_k
+
+GRID_CUT = (3, 4, 5, 6, 8, 10, 12, 15, 20, 25, 30)
+GRID_HF = (0.5, 0.6, 0.7, 0.8, 0.9, 1.0)
+CUT_LO, CUT_SPAN = 3.0, 27.0
+HF_LO, HF_SPAN = 0.5, 0.5
+
+
+def init_weights(seed: int = 0) -> np.ndarray:
+    """He-initialised weights, packed W1, b1, W2, b2, W3, b3; the last layer is
+    zeroed so the untrained network predicts the middle of both ranges."""
+    rng = np.random.default_rng(seed)
+    w1 = rng.standard_normal((128, 64)) * np.sqrt(2.0 / 64)
+    w2 = rng.standard_normal((64, 128)) * np.sqrt(2.0 / 128)
+    parts = [w1.ravel(), np.zeros(128), w2.ravel(), np.zeros(64), np.zeros(2 * 64), np.zeros(2)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def label_queries(index, queries: DeviceCSR, k: int = 10, target: float = 0.9, quantized: bool = True,
+                  grid_cut=GRID_CUT, grid_hf=GRID_HF, base_params: dict | None = None):
+    """Per-query (cut, heap_factor) labels: the grid point with the fewest
+    algorithmic bytes whose recall@k reaches `target`; queries that never reach
+    it take their highest-recall point.  Returns (cut, hf, table) where table
+    holds every grid point's per-query recall and bytes."""
+    base = dict(base_params or {})
+    _, gt = seismic_search_exact(index, queries, k)
+    gt = gt.cpu().numpy()
+    nq = queries.n_rows
+    best_bytes = np.full(nq, np.inf)
+    best_rec = np.full(nq, -1.0)
+    cut = np.full(nq, grid_cut[len(grid_cut) // 2], dtype=np.int64)
+    hf = np.full(nq, 0.8)
+    table = []
+    for c in grid_cut:
+        for h in grid_hf:
+            ids, sc, st = seismic_search(index, queries, search_params(k=k, cut=c, heap_factor=h,
+                                                                      max_query_nnz=queries.max_row_nnz,
+                                                                      **base), stats=True)
+            rec = recall_at_k(ids.cpu().numpy().view(np.uint32), sc.cpu().numpy(), gt, k)
+            by = algorithmic_bytes(st, k, quantized)
+            table.append((c, h, rec, by))
+            ok = rec >= target
+            better = ok & ((best_rec < target) | (by < best_bytes))
+            fallback = (~ok) & (best_rec < target) & (rec > best_rec)
+            upd = better | fallback
+            cut[upd], hf[upd] = c, h
+            best_bytes[upd] = by[upd]
+            best_rec[upd] = rec[upd]
+    return cut, hf, table
+
+
+def targets_from_labels(cut, hf) -> np.ndarray:
+    t0 = (np.asarray(cut, dtype=np.float64) - CUT_LO) / CUT_SPAN
+    t1 = (np.asarray(hf, dtype=np.float64) - HF_LO) / HF_SPAN
+    return np.clip(np.stack([t0, t1], axis=1), 0.0, 1.0).astype(np.float32)
+
+
+def train(features: np.ndarray, targets: np.ndarray, steps: int = 3000, lr: float = 2e-3, batch: int = 4096,
+          seed: int = 0, weights: np.ndarray | None = None, log_every: int = 0):
+    """Adam on the device with the library's MLP kernels; returns the weights
+    (host float32) and the loss trace."""
+    import torch
+    dev = "cuda"
+    rng = np.random.default_rng(seed)
+    # feature scaling is part of the data, not the network: keep raw features
+    f_all = torch.from_numpy(np.ascontiguousarray(features, dtype=np.float32)).to(dev)
+    t_all = torch.from_numpy(np.ascontiguousarray(targets, dtype=np.float32)).to(dev)
+    w = torch.from_numpy(weights if weights is not None else init_weights(seed)).to(dev)
+    g = torch.zeros_like(w)
+    m = torch.zeros_like(w)
+    v = torch.zeros_like(w)
+    loss = torch.zeros(1, device=dev)
+    n = f_all.shape[0]
+    trace = []
+    for step in range(1, steps + 1):
+        if batch < n:
+            idx = torch.from_numpy(rng.choice(n, size=batch, replace=False)).to(dev)
+            f, t = f_all.index_select(0, idx).contiguous(), t_all.index_select(0, idx).contiguous()
+        else:
+            f, t = f_all, t_all
+        seismic_mlp_train_step(w, g, m, v, f, t, lr, step, loss)
+        if log_every and step % log_every == 0:
+            trace.append((step, float(loss.item())))
+    torch.cuda.synchronize()
+    trace.append((steps, float(loss.item())))
+    return w.cpu().numpy(), trace
+
+
+def predict(weights: np.ndarray, features: np.ndarray):
+    """(cut, heap_factor) the device MLP predicts (same mapping as the search)."""
+    import torch
+    w = torch.from_numpy(np.ascontiguousarray(weights, dtype=np.float32)).cuda()
+    f = torch.from_numpy(np.ascontiguousarray(features, dtype=np.float32)).cuda()
+    out = torch.empty((f.shape[0], 2), device="cuda")
+    seismic_mlp_forward(w, f, out)
+    o = out.cpu().numpy().astype(np.float64)
+    s = 1.0 / (1.0 + np.exp(-o))
+    cut = np.clip(np.rint(CUT_LO + CUT_SPAN * s[:, 0]), 3, 30).astype(np.int64)
+    hf = HF_LO + HF_SPAN * s[:, 1]
+    return cut, hf
+
+
+def fit(index, train_queries: DeviceCSR, host_train_queries, k: int = 10, target: float = 0.9,
+        quantized: bool = True, steps: int = 3000, lr: float = 2e-3, seed: int = 0, base_params=None):
+    """Labels, features, training; installs the network in the index."""
+    cut, hf, table = label_queries(index, train_queries, k, target, quantized, base_params=base_params)
+    feats = seismic_query_features(index, host_train_queries)
+    w, trace = train(feats, targets_from_labels(cut, hf), steps=steps, lr=lr, seed=seed)
+    seismic_set_mlp(index, w)
+    return dict(weights=w, trace=trace, label_cut=cut, label_hf=hf, table=table, features=feats)

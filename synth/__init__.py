@@ -135,8 +135,10 @@ def generate(n: int, *, seed: int, stream: int, d: int = VOCAB, K: int = 64, zip
     return CSR(indptr, terms, vals, d)
 
 
-# Streams: documents and each query set draw from disjoint streams of one seed.
-DOC_STREAM, QUERY_STREAM = 1, 2
+# Streams: documents and each query set draw from disjoint streams of one seed
+# (one seed fixes the topic model they all share): the evaluation queries,
+# training queries for the parameter model, a held-out set, serving arrivals.
+DOC_STREAM, QUERY_STREAM, TRAIN_STREAM, HELDOUT_STREAM, SERVE_STREAM = 1, 2, 3, 4, 5
 
 
 def docs(n: int, seed: int = 0, d: int = VOCAB, **kw) -> CSR:
