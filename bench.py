@@ -38,12 +38,13 @@ WORKLOADS = {
     "c2": dict(desc="Seismic 1M docs, vocab 30522, lambda=6000, beta=400, alpha=0.4, u8 summaries, "
                     "10k queries (uniform nnz 10-150), k=10, grid cut {5,10,20} x hf {0.6..0.9}",
                n_docs=1_000_000, n_q=10_000, uneven=True, lam=6000, beta=400, alpha=0.4, quant=True,
-               cuts=(5, 10, 20), hfs=(0.6, 0.7, 0.8, 0.9), kappa=0, cpu_sample=200, n_train=20_000),
+               cuts=(5, 10, 20), hfs=(0.6, 0.7, 0.8, 0.9), kappa=0, cpu_sample=200, n_train=20_000,
+               serve_rates=(5_000, 50_000, 100_000, 200_000)),
     # the c2 shape at 300k documents and 2k queries: small enough for multi-pass ncu captures
     "c2s": dict(desc="Seismic 300k docs, vocab 30522, lambda=6000, beta=400, alpha=0.4, u8 summaries, "
                      "2k queries (uniform nnz 10-150), k=10, cut=5, heap_factor=0.9", n_docs=300_000, n_q=2000,
                 uneven=True, lam=6000, beta=400, alpha=0.4, quant=True, cuts=(5,), hfs=(0.9,), kappa=0,
-                cpu_sample=100, n_train=4000),
+                cpu_sample=100, n_train=4000, serve_rates=(20_000, 200_000)),
     "c3": dict(desc="Seismic 8.8M docs, vocab 30522, lambda=6000, beta=400, alpha=0.4, u8 summaries, kappa=10, "
                     "10k queries (uniform nnz 10-150), k=10", n_docs=8_800_000, n_q=10_000, uneven=True, lam=6000,
                beta=400, alpha=0.4, quant=True, cuts=(5, 10, 20), hfs=(0.6, 0.7, 0.8, 0.9), kappa=10,
@@ -187,7 +188,34 @@ def learned_eval(args, w, sz, ix, dq, gt_sc, stream, time_runs):
     return {"value": lr["qps"], "unit": "queries/s", "recall@10": lr["recall"], "ms_per_step": lr["ms"],
             "fixed_at_equal_recall": ref, "qps_gain_vs_fixed": lr["qps"] / ref["qps"],
             "train_queries": tq.n_rows, "label_target_recall": args.learn_target, "fit_seconds": t_fit,
-            "final_loss": res["trace"][-1][1], "fixed_fine_grid": fine}
+            "final_loss": res["trace"][-1][1], "label_mean_recall": res["label_recall"],
+            "calibration_shift": res["calib_shift"], "validation_recall": res["val_recall"],
+            "fixed_fine_grid": fine}
+
+
+def serving_eval(args, w, sz, ix, best, learned):
+    """Poisson arrivals replayed through the continuous-batching server:
+    p50/p99 latency (arrival to results on the host) and achieved QPS per
+    offered rate, with recall@10 of the served k=10 requests."""
+    import synth
+    from paper_2509_24815_gb300 import metrics, serve
+    sp = sz.search_params(cut=best["cut"], heap_factor=best["heap_factor"], learned=learned, shape=args.shape,
+                          wave=args.wave, persistent=bool(args.persistent), use_knn=bool(w["kappa"]))
+    srv = sz.Server(ix, sp, max_batch=512, streams=4, max_query_nnz=160)
+    out = []
+    for rate in w["serve_rates"]:
+        n = int(min(20_000, max(2_000, rate * 2.0)))
+        q = synth.queries(n, seed=0, uneven=True, stream=synth.SERVE_STREAM)
+        ids, sc, kq, summ = serve.run_trace(ix, q, rate, search=sp, server=srv)
+        gi, gs = sz.seismic_search_exact(ix, q, K)
+        m10 = kq == 10
+        rec = metrics.recall_at_k(ids[m10][:, :K], sc[m10][:, :K], gs[m10], K).mean() if m10.any() else None
+        summ["recall@10_k10_requests"] = float(rec) if rec is not None else None
+        out.append(summ)
+        log(f"serving {rate:>9,.0f} q/s offered: achieved {summ['achieved_qps']:,.0f} q/s, "
+            f"p50 {summ['p50_ms']:.3f} ms, p99 {summ['p99_ms']:.3f} ms, recall@10 {summ['recall@10_k10_requests']:.4f}")
+    srv.close()
+    return {"params": "learned (fixed fallback)" if learned else "fixed", "rates": out}
 
 
 def run_reference(args, w):
@@ -222,6 +250,7 @@ def main():
     ap.add_argument("--persistent", type=int, default=1)
     ap.add_argument("--shape", type=int, default=1, help="1: CTA per query, 2: warp per query, 0: auto")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--learn-target", type=float, default=0.9)
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
@@ -369,6 +398,8 @@ def main():
     }
     if not args.no_learned and w.get("n_train"):
         line["learned"] = learned_eval(args, w, sz, ix, dq, gt_sc, stream, time_runs)
+    if not args.no_serve and w.get("serve_rates"):
+        line["serving"] = serving_eval(args, w, sz, ix, best, bool(line.get("learned")))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(w, docs, queries, best["cut"], best["heap_factor"])
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}

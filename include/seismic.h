@@ -245,6 +245,51 @@ int seismic_mlp_train_step(float *weights, float *grads, float *adam_m, float *a
                            const float *features, const float *targets, uint64_t n, float lr,
                            uint32_t step, float *loss_out, void *stream);
 
+/* Continuous-batching server (not in the paper, whose queries run one at a
+ * time on one CPU thread).  Requests queue on the host; progress() reaps
+ * finished batches and admits waiting requests as soon as a stream and device
+ * slots are free, so requests that arrive while others run start without
+ * waiting for them, and their work overlaps on the GPU.  Each stream has its
+ * own workspace and pinned staging buffers; the index is shared read-only, so
+ * a request's result is the same alone and in the mix. */
+typedef struct seismic_server seismic_server;
+typedef struct {
+  uint32_t max_batch;     /* requests per launch; 0 = 256 */
+  uint32_t streams;       /* batches in flight at once (1..64); 0 = 4 */
+  uint32_t max_query_nnz; /* admission: longer requests are refused; 0 = 1024 */
+  uint32_t slot_budget;   /* admission: requests on the device at once; 0 = what the search kernel's
+                             shared memory per query (query, block scores, a 100-entry heap) lets
+                             stay resident: CTAs per SM x SMs */
+} seismic_server_params;
+
+/* Creates a server over `index` (which must outlive it).  `search` fixes the
+ * search parameters (its k is replaced per request); every stream's workspace
+ * is sized by one warm-up batch, so serving does not allocate device memory.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int seismic_server_create(seismic_index *index, const seismic_search_params *search,
+                          const seismic_server_params *params, seismic_server **out);
+/* Queues one host query (ascending terms) for top-k; `ticket` identifies it.
+ * The arrival time is now.  Errors: EINVAL (malformed, too long). */
+int seismic_server_submit(seismic_server *srv, const uint16_t *terms, const float *vals, uint32_t nnz, uint32_t k,
+                          uint64_t *ticket);
+/* Non-blocking: reaps finished batches, launches admitted ones.  `completed`
+ * (may be NULL) receives how many requests finished in this call. */
+int seismic_server_progress(seismic_server *srv, uint32_t *completed);
+/* If the request is done (*done = 1): copies its k ids/scores (caller-owned
+ * host buffers, may be NULL), its arrival-to-completion latency in
+ * microseconds, and forgets it.  Otherwise *done = 0.  EINVAL: unknown ticket. */
+int seismic_server_result(seismic_server *srv, uint64_t ticket, uint32_t *ids, float *scores, double *latency_us,
+                          int32_t *done);
+/* Replays an arrival trace in a tight host loop: query i (host CSR row i)
+ * arrives arrival_s[i] seconds after the start (non-decreasing) asking for
+ * top-k_per_query[i]; results go to ids_out/scores_out[n * k_stride] (rows
+ * padded past their k), latencies to latency_us[n] (from the scheduled
+ * arrival), the elapsed time to *wall_s (may be NULL). */
+int seismic_server_replay(seismic_server *srv, const seismic_csr *queries, const double *arrival_s,
+                          const uint32_t *k_per_query, uint32_t k_stride, uint32_t *ids_out, float *scores_out,
+                          double *latency_us, double *wall_s);
+void seismic_server_destroy(seismic_server *srv);
+
 /* Query processing that allocates no memory (this entry point has no
  * counterpart in the paper; it is for callers that cannot allocate device
  * memory while they serve queries: a process whose memory pool is fixed at

@@ -69,6 +69,11 @@ class IndexInfo(ctypes.Structure):
                 ("has_mlp", ctypes.c_int32), ("device_bytes", ctypes.c_uint64)]
 
 
+class ServerParams(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_uint32), ("streams", ctypes.c_uint32), ("max_query_nnz", ctypes.c_uint32),
+                ("slot_budget", ctypes.c_uint32)]
+
+
 _vp, _u64, _u32, _i32, _f32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32, ctypes.c_float
 _P = ctypes.POINTER
 _SIGS = {
@@ -87,6 +92,12 @@ _SIGS = {
     "seismic_mlp_forward": ([_vp, _vp, _u64, _vp, _vp], ctypes.c_int),
     "seismic_mlp_train_step": ([_vp, _vp, _vp, _vp, _vp, _vp, _u64, _f32, _u32, _vp, _vp], ctypes.c_int),
     "seismic_search_noalloc": ([_vp, _P(_CSR), _P(SearchParams), _vp, _vp, _vp], ctypes.c_int),
+    "seismic_server_create": ([_vp, _P(SearchParams), _P(ServerParams), _P(_vp)], ctypes.c_int),
+    "seismic_server_submit": ([_vp, _vp, _vp, _u32, _u32, _P(_u64)], ctypes.c_int),
+    "seismic_server_progress": ([_vp, _P(_u32)], ctypes.c_int),
+    "seismic_server_result": ([_vp, _u64, _vp, _vp, _P(ctypes.c_double), _P(_i32)], ctypes.c_int),
+    "seismic_server_replay": ([_vp, _P(_CSR), _vp, _vp, _u32, _vp, _vp, _vp, _P(ctypes.c_double)], ctypes.c_int),
+    "seismic_server_destroy": ([_vp], None),
     "seismic_free": ([_vp], None),
     "seismic_last_error": ([], ctypes.c_char_p),
     "seismic_version": ([], ctypes.c_char_p),
@@ -335,6 +346,67 @@ def seismic_search_noalloc(index: Index, queries: DeviceCSR, params: SearchParam
     s, keep = _csr_struct(queries)
     _check(_lib.seismic_search_noalloc(index.handle, ctypes.byref(s), ctypes.byref(params), ids_out.data_ptr(),
                                        scores_out.data_ptr(), _stream_ptr(stream)))
+
+
+class Server:
+    """Continuous-batching server over an index (seismic_server_*)."""
+
+    def __init__(self, index: Index, search: SearchParams | None = None, max_batch=256, streams=4,
+                 max_query_nnz=1024, slot_budget=0):
+        self.index = index  # kept alive for the server's lifetime
+        sp = search if search is not None else search_params()
+        pp = ServerParams(int(max_batch), int(streams), int(max_query_nnz), int(slot_budget))
+        h = ctypes.c_void_p()
+        _check(_lib.seismic_server_create(index.handle, ctypes.byref(sp), ctypes.byref(pp), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if self._h and self._h.value:
+            _lib.seismic_server_destroy(self._h)
+            self._h = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, terms, vals, k=10) -> int:
+        t = np.ascontiguousarray(terms, dtype=np.uint16)
+        v = np.ascontiguousarray(vals, dtype=np.float32)
+        tk = ctypes.c_uint64()
+        _check(_lib.seismic_server_submit(self._h, t.ctypes.data, v.ctypes.data, len(t), int(k), ctypes.byref(tk)))
+        return tk.value
+
+    def progress(self) -> int:
+        n = ctypes.c_uint32()
+        _check(_lib.seismic_server_progress(self._h, ctypes.byref(n)))
+        return n.value
+
+    def result(self, ticket: int, k: int):
+        """(ids, scores, latency_us) once done, else None."""
+        ids = np.empty(k, dtype=np.uint32)
+        sc = np.empty(k, dtype=np.float32)
+        lat = ctypes.c_double()
+        done = ctypes.c_int32()
+        _check(_lib.seismic_server_result(self._h, ticket, ids.ctypes.data, sc.ctypes.data, ctypes.byref(lat),
+                                          ctypes.byref(done)))
+        return (ids, sc, lat.value) if done.value else None
+
+    def replay(self, queries, arrival_s, k_per_query):
+        """Replays an arrival trace; returns (ids, scores, latency_us, wall_s)."""
+        s, keep = _csr_struct(queries)
+        arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        ks = np.ascontiguousarray(k_per_query, dtype=np.uint32)
+        kst = int(ks.max()) if len(ks) else 1
+        n = len(arr)
+        ids = np.empty((n, kst), dtype=np.uint32)
+        sc = np.empty((n, kst), dtype=np.float32)
+        lat = np.empty(n, dtype=np.float64)
+        wall = ctypes.c_double()
+        _check(_lib.seismic_server_replay(self._h, ctypes.byref(s), arr.ctypes.data, ks.ctypes.data, kst,
+                                          ids.ctypes.data, sc.ctypes.data, lat.ctypes.data, ctypes.byref(wall)))
+        return ids, sc, lat, wall.value
 
 
 def seismic_free(index: Index):

@@ -110,15 +110,16 @@ struct Staged {
 
 // Puts the queries on the device (copying host ones into the workspace) and
 // finds the largest row.
-int stage_queries(seismic_index *ix, const seismic_csr *q, uint32_t bound, cudaStream_t st, Staged &out) {
+int stage_queries(seismic_index *ix, Workspace *w, const seismic_csr *q, uint32_t bound, cudaStream_t st,
+                  Staged &out) {
   if (!q->on_device) {
     int rc = validate_host_csr(q, "queries", ix->dim);
     if (rc) return rc;
     uint64_t nnz = q->indptr[q->n_rows], mx = 0;
     for (uint64_t i = 0; i < q->n_rows; i++) mx = std::max<uint64_t>(mx, q->indptr[i + 1] - q->indptr[i]);
     size_t b_ip = (q->n_rows + 1) * 8, b_t = ((nnz * 2 + 15) / 16) * 16, b_v = nnz * 4;
-    if ((rc = ix->ws_q.ensure(b_ip + b_t + b_v + 64))) return rc;
-    uint8_t *base = ix->ws_q.as<uint8_t>();
+    if ((rc = w->q.ensure(b_ip + b_t + b_v + 64))) return rc;
+    uint8_t *base = w->q.as<uint8_t>();
     SZ_CUDA(cudaMemcpyAsync(base, q->indptr, b_ip, cudaMemcpyHostToDevice, st));
     if (nnz) {
       SZ_CUDA(cudaMemcpyAsync(base + b_ip, q->terms, nnz * 2, cudaMemcpyHostToDevice, st));
@@ -138,9 +139,9 @@ int stage_queries(seismic_index *ix, const seismic_csr *q, uint32_t bound, cudaS
     out.maxnnz = bound;
     return SEISMIC_OK;
   }
-  int rc = ix->ws_queue.ensure(64);
+  int rc = w->queue.ensure(64);
   if (rc) return rc;
-  uint32_t *m = ix->ws_queue.as<uint32_t>() + 4;
+  uint32_t *m = w->queue.as<uint32_t>() + 4;
   SZ_CUDA(cudaMemsetAsync(m, 0, 4, st));
   k_max_row_nnz<<<std::max<uint64_t>(1, std::min<uint64_t>(1024, (q->n_rows + 255) / 256)), 256, 0, st>>>(q->indptr, q->n_rows, m);
   SZ_CUDA(cudaGetLastError());
@@ -175,9 +176,9 @@ int check_params(const seismic_index *ix, const seismic_search_params *p) {
 
 }  // namespace
 
-int search_impl(seismic_index *ix, const seismic_csr *queries, const seismic_search_params *p, uint32_t *ids_out,
-                float *scores_out, int32_t out_on_device, void *stream, uint64_t *stats) {
-  if (!ix || !queries) return fail(SEISMIC_EINVAL, "NULL index/queries");
+int search_ws(seismic_index *ix, Workspace *w, const seismic_csr *queries, const seismic_search_params *p,
+              uint32_t *ids_out, float *scores_out, int32_t out_on_device, void *stream, uint64_t *stats) {
+  if (!ix || !queries || !w) return fail(SEISMIC_EINVAL, "NULL index/queries");
   int rc = check_params(ix, p);
   if (rc) return rc;
   if (!ids_out || !scores_out) return fail(SEISMIC_EINVAL, "NULL outputs");
@@ -187,20 +188,20 @@ int search_impl(seismic_index *ix, const seismic_csr *queries, const seismic_sea
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const uint32_t nq = (uint32_t)queries->n_rows, k = p->k;
   Staged q;
-  if ((rc = stage_queries(ix, queries, p->max_query_nnz, st, q))) return rc;
+  if ((rc = stage_queries(ix, w, queries, p->max_query_nnz, st, q))) return rc;
   uint32_t *d_ids = ids_out;
   float *d_sc = scores_out;
   if (!out_on_device) {
-    if ((rc = ix->ws_out.ensure((size_t)nq * k * 8))) return rc;
-    d_ids = ix->ws_out.as<uint32_t>();
+    if ((rc = w->out.ensure((size_t)nq * k * 8))) return rc;
+    d_ids = w->out.as<uint32_t>();
     d_sc = reinterpret_cast<float *>(d_ids + (size_t)nq * k);
   }
-  if ((rc = ix->ws_queue.ensure(64))) return rc;
-  SZ_CUDA(cudaMemsetAsync(ix->ws_queue.p, 0, 16, st));
+  if ((rc = w->queue.ensure(64))) return rc;
+  SZ_CUDA(cudaMemsetAsync(w->queue.p, 0, 16, st));
   unsigned long long *d_stats = nullptr;
   if (stats) {
-    if ((rc = ix->ws_stats.ensure((size_t)nq * SEISMIC_STATS_N * 8))) return rc;
-    d_stats = ix->ws_stats.as<unsigned long long>();
+    if ((rc = w->stats.ensure((size_t)nq * SEISMIC_STATS_N * 8))) return rc;
+    d_stats = w->stats.as<unsigned long long>();
   }
   SearchArgs a{};
   a.fwd_cptr = ix->fwd_cptr.as<uint32_t>();
@@ -235,7 +236,7 @@ int search_impl(seismic_index *ix, const seismic_csr *queries, const seismic_sea
   a.ids = d_ids;
   a.scores = d_sc;
   a.stats = d_stats;
-  a.queue = ix->ws_queue.as<uint32_t>();
+  a.queue = w->queue.as<uint32_t>();
   a.persistent = p->persistent ? 1 : 0;
   a.W = (ix->dim + 31) / 32;
   a.QN = std::max<uint32_t>(4, (q.maxnnz + 3) & ~3u);
@@ -247,8 +248,8 @@ int search_impl(seismic_index *ix, const seismic_csr *queries, const seismic_sea
   if (p->learned) {
     // (cut, heap_factor) per query from the MLP, fused ahead of the search
     size_t need = (size_t)nq * (SEISMIC_MLP_IN * 4 + 8);
-    if ((rc = ix->ws_params.ensure(need))) return rc;
-    float *feat = ix->ws_params.as<float>();
+    if ((rc = w->params.ensure(need))) return rc;
+    float *feat = w->params.as<float>();
     uint32_t *qc = reinterpret_cast<uint32_t *>(feat + (size_t)nq * SEISMIC_MLP_IN);
     float *qh = reinterpret_cast<float *>(qc + nq);
     if ((rc = launch_features(q.ip, q.t, q.v, nq, ix->list_ptr.as<uint32_t>(), ix->blk_ptr.as<uint32_t>(), ix->dim,
@@ -266,8 +267,8 @@ int search_impl(seismic_index *ix, const seismic_csr *queries, const seismic_sea
   a.prefetch = p->no_prefetch ? 0u : 256u;
   const bool warp_shape0 = p->shape == 2 || (p->shape == 0 && k <= 128 && a.wave <= 1);
   if (p->order == 0 && nq > 1 && (a.persistent || warp_shape0)) {
-    if ((rc = ix->ws_perm.ensure((size_t)nq * 12))) return rc;
-    unsigned long long *keys = ix->ws_perm.as<unsigned long long>();
+    if ((rc = w->perm.ensure((size_t)nq * 12))) return rc;
+    unsigned long long *keys = w->perm.as<unsigned long long>();
     uint32_t *perm = reinterpret_cast<uint32_t *>(keys + nq);
     k_order_keys<<<(nq + 255) / 256, 256, 0, st>>>(q.ip, q.t, q.v, nq, keys);
     SZ_CUDA(cudaGetLastError());
@@ -294,8 +295,8 @@ int search_impl(seismic_index *ix, const seismic_csr *queries, const seismic_sea
     uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((nq + wpb - 1) / wpb,
                                                                      (uint64_t)std::max(1, blocks) * sm_count(ix->device)));
     a.seen_words = (uint32_t)(((ix->n_docs + 31) / 32 + 3) & ~3ull);
-    if ((rc = ix->ws_seen.ensure((size_t)grid * wpb * a.seen_words * 4))) return rc;
-    a.seen_bm = ix->ws_seen.as<uint32_t>();
+    if ((rc = w->seen.ensure((size_t)grid * wpb * a.seen_words * 4))) return rc;
+    a.seen_bm = w->seen.as<uint32_t>();
     a.persistent = 1;
     if ((rc = launch_search_warp(a, group, smem, grid, wpb, st))) return rc;
   } else {
@@ -313,8 +314,8 @@ int search_impl(seismic_index *ix, const seismic_csr *queries, const seismic_sea
     if ((rc = search_occupancy(group, nw, smem, &blocks))) return rc;
     grid = (uint32_t)std::min<uint64_t>(nq, (uint64_t)std::max(1, blocks) * sm_count(ix->device));
     a.seen_words = (uint32_t)(((ix->n_docs + 31) / 32 + 3) & ~3ull);
-    if ((rc = ix->ws_seen.ensure((size_t)grid * a.seen_words * 4))) return rc;
-    a.seen_bm = ix->ws_seen.as<uint32_t>();
+    if ((rc = w->seen.ensure((size_t)grid * a.seen_words * 4))) return rc;
+    a.seen_bm = w->seen.as<uint32_t>();
   }
   if ((rc = launch_search(a, group, nw, smem, grid, st))) return rc;
   }
@@ -325,11 +326,17 @@ int search_impl(seismic_index *ix, const seismic_csr *queries, const seismic_sea
   if (stats) SZ_CUDA(cudaMemcpyAsync(stats, d_stats, (size_t)nq * SEISMIC_STATS_N * 8, cudaMemcpyDeviceToHost, st));
   if (!out_on_device || stats || !queries->on_device) {
     uint32_t err = 0;
-    SZ_CUDA(cudaMemcpyAsync(&err, ix->ws_queue.as<uint32_t>() + 1, 4, cudaMemcpyDeviceToHost, st));
+    SZ_CUDA(cudaMemcpyAsync(&err, w->queue.as<uint32_t>() + 1, 4, cudaMemcpyDeviceToHost, st));
     SZ_CUDA(cudaStreamSynchronize(st));
     if (err) return fail(SEISMIC_EINVAL, "queries: a query exceeded max_query_nnz or held a term >= dim");
   }
   return SEISMIC_OK;
+}
+
+int search_impl(seismic_index *ix, const seismic_csr *queries, const seismic_search_params *p, uint32_t *ids_out,
+                float *scores_out, int32_t out_on_device, void *stream, uint64_t *stats) {
+  if (!ix) return fail(SEISMIC_EINVAL, "NULL index");
+  return search_ws(ix, &ix->ws, queries, p, ids_out, scores_out, out_on_device, stream, stats);
 }
 
 int exact_impl(seismic_index *ix, const seismic_csr *queries, uint32_t k, uint32_t *ids_out, float *scores_out,
@@ -342,13 +349,14 @@ int exact_impl(seismic_index *ix, const seismic_csr *queries, uint32_t k, uint32
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const uint32_t nq = (uint32_t)queries->n_rows;
   Staged q;
-  int rc = stage_queries(ix, queries, 1, st, q);
+  Workspace *w = &ix->ws;
+  int rc = stage_queries(ix, w, queries, 1, st, q);
   if (rc) return rc;
   uint32_t *d_ids = ids_out;
   float *d_sc = scores_out;
   if (!out_on_device) {
-    if ((rc = ix->ws_out.ensure((size_t)nq * k * 8))) return rc;
-    d_ids = ix->ws_out.as<uint32_t>();
+    if ((rc = w->out.ensure((size_t)nq * k * 8))) return rc;
+    d_ids = w->out.as<uint32_t>();
     d_sc = reinterpret_cast<float *>(d_ids + (size_t)nq * k);
   }
   uint32_t grid = (uint32_t)std::min<uint64_t>(nq, 2ull * sm_count(ix->device));

@@ -99,7 +99,16 @@ constexpr uint32_t kChunkBytes = 48;
 constexpr uint32_t kMaxRowNnzBuild = 8192;  // clustering stages a centroid chunk in shared memory
 constexpr uint32_t kMaxK = 1024;
 
-struct MlpState;
+// Device memory one search call works in: one per concurrent stream.
+struct Workspace {
+  DevBuf q;       // staged host queries
+  DevBuf out;     // staged outputs
+  DevBuf stats;   // per-query work counters
+  DevBuf queue;   // persistent work counter, error word, scratch words
+  DevBuf params;  // learned mode: features and per-query (cut, heap_factor)
+  DevBuf seen;    // per-CTA (or per-warp) seen bitmaps
+  DevBuf perm;    // work-queue order keys and permutation
+};
 
 }  // namespace seismic
 
@@ -154,16 +163,10 @@ struct seismic_index {
   int has_mlp = 0;
   seismic::DevBuf mlp;       // f32[SEISMIC_MLP_PARAMS]
 
-  // search workspace (grown on demand)
-  seismic::DevBuf ws_q;      // staged host queries
-  seismic::DevBuf ws_out;    // staged outputs
-  seismic::DevBuf ws_stats;
-  seismic::DevBuf ws_queue;  // persistent-kernel work counter + error word
-  seismic::DevBuf ws_params; // per-query (cut, hf) for learned mode
-  seismic::DevBuf ws_feat;
+  // the default search workspace (grown on demand); concurrent searches on
+  // other streams bring their own
+  seismic::Workspace ws;
   seismic::DevBuf ws_exact;  // exact-search accumulators
-  seismic::DevBuf ws_seen;   // per-CTA seen bitmaps of persistent searches
-  seismic::DevBuf ws_perm;   // work-queue order keys and permutation
 };
 
 namespace seismic {

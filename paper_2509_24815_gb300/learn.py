@@ -67,6 +67,34 @@ def label_queries(index, queries: DeviceCSR, k: int = 10, target: float = 0.9, q
     return cut, hf, table
 
 
+def lagrangian_labels(table, target: float, margin: float = 0.01):
+    """Per-query labels that meet the target on average with the least work:
+    each query takes the grid point maximising recall - mu * bytes, and mu is
+    the largest value (bisection) whose mean recall still reaches
+    target + margin.  Returns (cut, hf, mean recall, mean bytes)."""
+    cuts = np.array([c for c, _, _, _ in table], dtype=np.int64)
+    hfs = np.array([h for _, h, _, _ in table], dtype=np.float64)
+    rec = np.stack([r for _, _, r, _ in table], axis=1)   # [nq, G]
+    by = np.stack([b for _, _, _, b in table], axis=1)    # [nq, G]
+    want = min(target + margin, float(rec.max(axis=1).mean()))
+
+    def choose(mu):
+        g = np.argmax(rec - mu * by, axis=1)
+        return g, float(rec[np.arange(len(g)), g].mean())
+
+    lo, hi = 0.0, 1.0 / max(float(by.min()), 1.0)  # mu = hi: recall is worth less than one byte
+    while choose(hi)[1] >= want and hi < 1e3:
+        hi *= 2.0
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        if choose(mid)[1] >= want:
+            lo = mid
+        else:
+            hi = mid
+    g, r = choose(lo)
+    return cuts[g], hfs[g], r, float(by[np.arange(len(g)), g].mean())
+
+
 def targets_from_labels(cut, hf) -> np.ndarray:
     t0 = (np.asarray(cut, dtype=np.float64) - CUT_LO) / CUT_SPAN
     t1 = (np.asarray(hf, dtype=np.float64) - HF_LO) / HF_SPAN
@@ -118,11 +146,42 @@ def predict(weights: np.ndarray, features: np.ndarray):
     return cut, hf
 
 
+def calibrate(index, weights: np.ndarray, queries: DeviceCSR, gt_scores, k: int, target: float,
+              quantized: bool, base_params=None, shifts=(0.0, 0.15, 0.3, 0.45, 0.6, 0.8, 1.0, 1.3, 1.6, 2.0)):
+    """Shifts the cut output's bias (logit units) so that the learned form's
+    mean recall on held-out training queries reaches `target`, taking the
+    smallest shift that does (the least work).  Returns (weights, shift, recall)."""
+    base = dict(base_params or {})
+    b3 = MLP_PARAMS - 2
+    best = None
+    for s in shifts:
+        w = weights.copy()
+        w[b3] += np.float32(s)
+        seismic_set_mlp(index, w)
+        ids, sc = seismic_search(index, queries, search_params(k=k, cut=10, heap_factor=0.8, learned=True,
+                                                               max_query_nnz=queries.max_row_nnz, **base))
+        rec = float(recall_at_k(ids.cpu().numpy().view(np.uint32), sc.cpu().numpy(), gt_scores, k).mean())
+        best = (w, s, rec)
+        if rec >= target:
+            break
+    return best
+
+
 def fit(index, train_queries: DeviceCSR, host_train_queries, k: int = 10, target: float = 0.9,
-        quantized: bool = True, steps: int = 3000, lr: float = 2e-3, seed: int = 0, base_params=None):
-    """Labels, features, training; installs the network in the index."""
-    cut, hf, table = label_queries(index, train_queries, k, target, quantized, base_params=base_params)
+        quantized: bool = True, steps: int = 3000, lr: float = 2e-3, seed: int = 0, base_params=None,
+        val_frac: float = 0.2):
+    """Labels (trade-off form), features, training on the first part of the
+    training queries, calibration on the rest; installs the network."""
+    cut0, hf0, table = label_queries(index, train_queries, k, target, quantized, base_params=base_params)
+    cut, hf, lab_rec, lab_bytes = lagrangian_labels(table, target)
     feats = seismic_query_features(index, host_train_queries)
-    w, trace = train(feats, targets_from_labels(cut, hf), steps=steps, lr=lr, seed=seed)
+    n = host_train_queries.n_rows
+    ntr = max(1, int(n * (1.0 - val_frac)))
+    w, trace = train(feats[:ntr], targets_from_labels(cut[:ntr], hf[:ntr]), steps=steps, lr=lr, seed=seed)
+    val_host = host_train_queries.slice(ntr, n)
+    val = DeviceCSR.from_host(val_host)
+    _, gt_val = seismic_search_exact(index, val, k)
+    w, shift, val_rec = calibrate(index, w, val, gt_val.cpu().numpy(), k, target, quantized, base_params)
     seismic_set_mlp(index, w)
-    return dict(weights=w, trace=trace, label_cut=cut, label_hf=hf, table=table, features=feats)
+    return dict(weights=w, trace=trace, label_cut=cut, label_hf=hf, label_recall=lab_rec, label_bytes=lab_bytes,
+                table=table, features=feats, calib_shift=shift, val_recall=val_rec)
