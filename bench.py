@@ -201,7 +201,7 @@ def serving_eval(args, w, sz, ix, best, learned):
     from paper_2509_24815_gb300 import metrics, serve
     sp = sz.search_params(cut=best["cut"], heap_factor=best["heap_factor"], learned=learned, shape=args.shape,
                           wave=args.wave, persistent=bool(args.persistent), use_knn=bool(w["kappa"]))
-    srv = sz.Server(ix, sp, max_batch=512, streams=4, max_query_nnz=160)
+    srv = sz.Server(ix, sp, max_batch=1024, streams=16, max_query_nnz=160)
     out = []
     for rate in w["serve_rates"]:
         n = int(min(20_000, max(2_000, rate * 2.0)))

@@ -354,6 +354,8 @@ class Server:
     def __init__(self, index: Index, search: SearchParams | None = None, max_batch=256, streams=4,
                  max_query_nnz=1024, slot_budget=0):
         self.index = index  # kept alive for the server's lifetime
+        self.settings = dict(max_batch=max_batch, streams=streams, max_query_nnz=max_query_nnz,
+                             slot_budget=slot_budget)
         sp = search if search is not None else search_params()
         pp = ServerParams(int(max_batch), int(streams), int(max_query_nnz), int(slot_budget))
         h = ctypes.c_void_p()

@@ -102,27 +102,38 @@ struct seismic_server {
 namespace {
 
 int launch_batch(seismic_server *srv, Slot &s) {
-  // requests with the front request's k, FIFO, within max_batch and the slot budget
+  // every waiting request with the oldest request's k (a batch shares k: the
+  // heap size sets the skip threshold, so mixing k would change results), in
+  // arrival order, within max_batch and the slot budget
   const uint32_t k = srv->pending.front().k;
-  uint32_t n = 0;
+  const uint32_t room = srv->budget > srv->inflight ? srv->budget - srv->inflight : 0;
+  const uint32_t cap = std::min(srv->pp.max_batch, room);
+  if (cap == 0) return SEISMIC_OK;
+  std::deque<Request> batch, rest;
   size_t nnz = 0;
-  for (const Request &r : srv->pending) {
-    if (r.k != k || n == srv->pp.max_batch || srv->inflight + n + 1 > srv->budget) break;
-    n++;
-    nnz += r.t.size();
+  for (Request &r : srv->pending) {
+    if (r.k == k && batch.size() < cap) {
+      nnz += r.t.size();
+      batch.push_back(std::move(r));
+    } else {
+      rest.push_back(std::move(r));
+    }
   }
-  if (n == 0) return SEISMIC_OK;
+  srv->pending.swap(rest);
+  const uint32_t n = (uint32_t)batch.size();
   int rc;
   if ((rc = s.h_ip.ensure(n + 1)) || (rc = s.h_t.ensure(nnz + 8)) || (rc = s.h_v.ensure(nnz + 4)) ||
       (rc = s.h_ids.ensure((size_t)n * k)) || (rc = s.h_sc.ensure((size_t)n * k)) ||
       (rc = s.d_ip.ensure((n + 1) * 8)) || (rc = s.d_t.ensure(nnz * 2 + 16)) || (rc = s.d_v.ensure(nnz * 4 + 16)) ||
-      (rc = s.d_ids.ensure((size_t)n * k * 4)) || (rc = s.d_sc.ensure((size_t)n * k * 4)))
+      (rc = s.d_ids.ensure((size_t)n * k * 4)) || (rc = s.d_sc.ensure((size_t)n * k * 4))) {
+    for (auto it = batch.rbegin(); it != batch.rend(); ++it) srv->pending.push_front(std::move(*it));
     return rc;
+  }
   s.tickets.clear();
   size_t o = 0;
   s.h_ip.p[0] = 0;
   for (uint32_t i = 0; i < n; i++) {
-    Request &r = srv->pending.front();
+    Request &r = batch[i];
     std::memcpy(s.h_t.p + o, r.t.data(), r.t.size() * 2);
     std::memcpy(s.h_v.p + o, r.v.data(), r.v.size() * 4);
     o += r.t.size();
@@ -130,7 +141,6 @@ int launch_batch(seismic_server *srv, Slot &s) {
     s.tickets.push_back(r.ticket);
     Result &res = srv->results[r.ticket];
     res.arrive = r.arrive;
-    srv->pending.pop_front();
   }
   SZ_CUDA(cudaMemcpyAsync(s.d_ip.p, s.h_ip.p, (n + 1) * 8, cudaMemcpyHostToDevice, s.st));
   if (nnz) {

@@ -33,5 +33,5 @@ def run_trace(index, queries, rate_qps: float, ks=(10, 100), probs=(0.9, 0.1), s
     lat_ms = lat / 1e3
     summary = {"offered_qps": rate_qps, "achieved_qps": n / wall, "p50_ms": float(np.percentile(lat_ms, 50)),
                "p99_ms": float(np.percentile(lat_ms, 99)), "mean_ms": float(lat_ms.mean()), "queries": n,
-               "k_mix": {int(k): float(p) for k, p in zip(ks, probs)}, "max_batch": max_batch, "streams": streams}
+               "k_mix": {int(k): float(p) for k, p in zip(ks, probs)}, **srv.settings}
     return ids, sc, kq, summary
