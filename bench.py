@@ -151,7 +151,7 @@ def cpu_baseline(w, docs, queries, cut, hf, steps=1):
                       f"thread; lists built untimed", "times_s": times}
 
 
-def learned_eval(args, w, sz, ix, dq, gt_sc, stream, time_runs):
+def learned_eval(args, w, sz, ix, dq, gt_sc, stream, time_runs, launch):
     """Trains the per-query parameter MLP on separate synthetic training
     queries (labels from the method's own runs), then measures the learned form
     on the benchmark's queries against the fixed form at equal recall."""
@@ -161,7 +161,7 @@ def learned_eval(args, w, sz, ix, dq, gt_sc, stream, time_runs):
     t = time.time()
     tq = synth.queries(w["n_train"], seed=0, uneven=w["uneven"], stream=synth.TRAIN_STREAM)
     dtq = sz.DeviceCSR.from_host(tq)
-    base = dict(shape=args.shape, wave=args.wave, persistent=bool(args.persistent))
+    base = dict(launch)
     res = learn.fit(ix, dtq, tq, k=K, target=args.learn_target, quantized=w["quant"], steps=3000, base_params=base)
     t_fit = time.time() - t
     log(f"learned: labels + training on {tq.n_rows} queries in {t_fit:.1f}s, final loss {res['trace'][-1][1]:.4f}")
@@ -193,14 +193,14 @@ def learned_eval(args, w, sz, ix, dq, gt_sc, stream, time_runs):
             "fixed_fine_grid": fine}
 
 
-def serving_eval(args, w, sz, ix, best, learned):
+def serving_eval(args, w, sz, ix, best, learned, launch):
     """Poisson arrivals replayed through the continuous-batching server:
     p50/p99 latency (arrival to results on the host) and achieved QPS per
     offered rate, with recall@10 of the served k=10 requests."""
     import synth
     from paper_2509_24815_gb300 import metrics, serve
-    sp = sz.search_params(cut=best["cut"], heap_factor=best["heap_factor"], learned=learned, shape=args.shape,
-                          wave=args.wave, persistent=bool(args.persistent), use_knn=bool(w["kappa"]))
+    sp = sz.search_params(cut=best["cut"], heap_factor=best["heap_factor"], learned=learned,
+                          use_knn=bool(w["kappa"]), **launch)
     srv = sz.Server(ix, sp, max_batch=1024, streams=16, max_query_nnz=160)
     out = []
     for rate in w["serve_rates"]:
@@ -244,7 +244,7 @@ def main():
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--group", type=int, default=8)
+    ap.add_argument("--group", type=int, default=1, help="1: chunk-flattened scoring, 8/16/32: lane groups")
     ap.add_argument("--cta-warps", type=int, default=0)
     ap.add_argument("--wave", type=int, default=16)
     ap.add_argument("--persistent", type=int, default=1)
@@ -252,6 +252,9 @@ def main():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--learn-target", type=float, default=0.9)
+    ap.add_argument("--prefetch", type=int, default=0, help="TMA L2 prefetch of the wave's rows (when not autotuned)")
+    ap.add_argument("--autotune", type=int, default=1, help="tune the launch configuration at the operating point")
+    ap.add_argument("--graph", type=int, default=1, help="time the step as a CUDA graph replay")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -272,7 +275,7 @@ def main():
             dist.barrier()
 
     import paper_2509_24815_gb300 as sz
-    from paper_2509_24815_gb300 import metrics
+    from paper_2509_24815_gb300 import autotune, metrics
 
     docs, queries = make_data(w)
     t = time.time()
@@ -300,17 +303,20 @@ def main():
     def params(cut, hf):
         return sz.search_params(k=K, cut=cut, heap_factor=hf, use_knn=bool(w["kappa"]), wave=args.wave,
                                 group=args.group, cta_warps=args.cta_warps, persistent=bool(args.persistent),
-                                max_query_nnz=dq.max_row_nnz, shape=args.shape)
+                                max_query_nnz=dq.max_row_nnz, shape=args.shape, no_prefetch=not args.prefetch)
 
     def run(p):
         sz.seismic_search(ix, dq, p, ids_out=ids, scores_out=sc, stream=stream)
 
-    def time_runs(p, n):
+    def time_runs(p, n, fn=None):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * n)]
         with torch.cuda.stream(stream):
             for i in range(n):
                 ev[2 * i].record(stream)
-                run(p)
+                if fn is None:
+                    run(p)
+                else:
+                    fn()
                 ev[2 * i + 1].record(stream)
         stream.synchronize()
         return [ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(n)]
@@ -329,6 +335,26 @@ def main():
     ok = [g for g in grid if g["recall"] >= RECALL_TARGET]
     best = max(ok, key=lambda g: g["qps"]) if ok else max(grid, key=lambda g: g["recall"])
     p = params(best["cut"], best["heap_factor"])
+    launch = dict(shape=args.shape, group=args.group, cta_warps=args.cta_warps, wave=args.wave,
+                  persistent=bool(args.persistent), no_prefetch=not args.prefetch)
+    tuned = None
+    if args.autotune:
+        # launch configuration (kernel shape, lane group, warps, wave) at the chosen operating point
+        base = dict(k=K, cut=best["cut"], heap_factor=best["heap_factor"], use_knn=bool(w["kappa"]))
+        floor = min(RECALL_TARGET, best["recall"])
+
+        def rec_fn(i, s):
+            return metrics.recall_at_k(i.cpu().numpy().view(np.uint32), s.cpu().numpy(), gt_sc, K).mean()
+        kw, table = autotune.autotune(ix, dq, base, recall_fn=rec_fn, min_recall=floor, stream=stream, log=log)
+        launch = {x: kw[x] for x in launch}
+        p = sz.search_params(max_query_nnz=dq.max_row_nnz, **dict(base, **launch))
+        run(p)
+        stream.synchronize()
+        best["recall"] = float(rec_fn(ids, sc))
+        tuned = {"chosen": launch, "candidates": len(table),
+                 "table": [{x: t.get(x) for x in ("shape", "group", "cta_warps", "wave", "no_prefetch", "ms", "recall")}
+                           for t in table]}
+        log(f"autotune: {launch}, recall@10 {best['recall']:.4f}")
 
     # work counters for the algorithmic byte count (deterministic at wave = 1)
     _, _, st = sz.seismic_search(ix, dq, p, stats=True)
@@ -337,12 +363,28 @@ def main():
     for _ in range(args.warmup):
         run(p)
     stream.synchronize()
+    step, graph_note = (lambda: run(p)), "direct launches"
+    if args.graph:
+        # the whole step (queue reset, work-queue order, search) as one CUDA graph
+        g = torch.cuda.CUDAGraph()
+        try:
+            with torch.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
+                run(p)
+            stream.synchronize()
+            step, graph_note = g.replay, "CUDA graph replay"
+            for _ in range(args.warmup):
+                with torch.cuda.stream(stream):
+                    step()
+            stream.synchronize()
+        except Exception as e:  # capture unsupported here: direct launches of the same kernels
+            graph_note = f"direct launches (graph capture failed: {e})"
+            log(graph_note)
     clocks = Clocks(local)
     clocks.start()
     time.sleep(0.3)
     barrier()
     torch.cuda.synchronize()
-    per = time_runs(p, args.steps)  # events bracket each step's launch on its stream
+    per = time_runs(p, args.steps, step)  # events bracket each step on its stream
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
@@ -360,8 +402,7 @@ def main():
     hid = torch.empty((queries.n_rows, K), dtype=torch.int32).pin_memory()
     hsc = torch.empty((queries.n_rows, K), dtype=torch.float32).pin_memory()
     pe = sz.search_params(k=K, cut=best["cut"], heap_factor=best["heap_factor"], use_knn=bool(w["kappa"]),
-                          wave=args.wave, group=args.group, cta_warps=args.cta_warps,
-                          persistent=bool(args.persistent), shape=args.shape)
+                          **launch)
     for _ in range(2):
         sz.seismic_search(ix, hq, pe, ids_out=hid, scores_out=hsc, stream=stream)
     e2e_t = []
@@ -373,6 +414,8 @@ def main():
     h2d = queries.indptr.nbytes + queries.terms.nbytes + queries.vals.nbytes
     d2h = hid.numel() * 4 + hsc.numel() * 4
 
+    # kernels per step: the search, plus the work-queue order (keys, sort) ahead of a persistent launch
+    launches_per_step = 1 + (2 if (launch["persistent"] or launch["shape"] == 2) and dq.n_rows > 1 else 0)
     peak, peak_kind = peaks()
     achieved = alg_bytes / (float(np.mean(per)) * 1e-3) / 1e9  # this rank's kernel, per launch
     line = {
@@ -382,24 +425,23 @@ def main():
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": w["desc"], "cut": best["cut"], "heap_factor": best["heap_factor"],
                    "recall@10": best["recall"], "queries_per_step": dq.n_rows, "k": K,
-                   "l2": "index resident in HBM, larger than L2 (no flush)", "group": args.group,
-                   "cta_warps": args.cta_warps, "wave": args.wave, "persistent": args.persistent,
-                   "shape": args.shape,
-                   "parallelism": f"replicas x{world}"},
+                   "l2": "index resident in HBM, larger than L2 (no flush)", **launch,
+                   "launch": graph_note, "parallelism": f"replicas x{world}"},
         "grid": grid,
+        "autotune": tuned,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "peak_source": peak_kind,
                      "alg_bytes_per_launch": alg_bytes, "kernel": "k_search"},
         "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * launches_per_step,
         "clocks": clk,
         "index": {k: info[k] for k in ("n_docs", "nnz", "n_postings", "n_blocks", "n_summary_entries",
                                        "device_bytes")},
     }
     if not args.no_learned and w.get("n_train"):
-        line["learned"] = learned_eval(args, w, sz, ix, dq, gt_sc, stream, time_runs)
+        line["learned"] = learned_eval(args, w, sz, ix, dq, gt_sc, stream, time_runs, launch)
     if not args.no_serve and w.get("serve_rates"):
-        line["serving"] = serving_eval(args, w, sz, ix, best, bool(line.get("learned")))
+        line["serving"] = serving_eval(args, w, sz, ix, best, bool(line.get("learned")), launch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(w, docs, queries, best["cut"], best["heap_factor"])
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}

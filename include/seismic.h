@@ -93,7 +93,11 @@ typedef struct {
                             predictions fall back to (cut, heap_factor) above */
   uint32_t wave;         /* blocks evaluated per threshold update; 1 (default) keeps the
                             sequential visiting order of the algorithm exactly */
-  uint32_t group;        /* lanes cooperating on one document row: 8, 16 or 32; 0 = 8 */
+  uint32_t group;        /* how documents are scored.  CTA shape: 1 = every thread of the CTA
+                            takes row chunks of the whole wave (chunk-flattened; seen documents
+                            are dropped before their rows are read), 8/16/32 = lane groups of
+                            that width score one row each.  Warp shape: 4/8/16/32 lanes per
+                            row.  0 = 8.  Scores differ only in fp32 summation order */
   uint32_t cta_warps;    /* warps per CTA: 4, 8 or 16; 0 = 8 */
   uint32_t persistent;   /* 1: one persistent launch that pulls queries from a device queue */
   uint32_t max_query_nnz; /* device queries: an upper bound on any query's nonzeros, which sizes

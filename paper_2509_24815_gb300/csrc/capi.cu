@@ -164,8 +164,8 @@ int check_params(const seismic_index *ix, const seismic_search_params *p) {
   uint32_t g = p->group ? p->group : 8, w = p->cta_warps ? p->cta_warps : 8;
   if (p->shape > 2) return fail(SEISMIC_EINVAL, "shape must be 0 (auto), 1 (CTA per query) or 2 (warp per query)");
   const bool ws = p->shape == 2 || (p->shape == 0 && p->k <= 128 && p->wave <= 1);
-  if (!(g == 8 || g == 16 || g == 32 || (ws && g == 4)))
-    return fail(SEISMIC_EINVAL, "group must be 8/16/32 (4 also for the warp shape)");
+  if (!(g == 8 || g == 16 || g == 32 || (ws && g == 4) || (!ws && g == 1)))
+    return fail(SEISMIC_EINVAL, "group must be 8/16/32 (4 also for the warp shape, 1 for the CTA shape)");
   const uint32_t ww = p->cta_warps ? p->cta_warps : 4;
   if (ws ? !(ww == 1 || ww == 2 || ww == 4) : !(w == 4 || w == 8 || w == 16))
     return fail(SEISMIC_EINVAL, "cta_warps must be 1/2/4 (warp shape) or 4/8/16 (CTA shape)");
@@ -300,6 +300,7 @@ int search_ws(seismic_index *ix, Workspace *w, const seismic_csr *queries, const
     a.persistent = 1;
     if ((rc = launch_search_warp(a, group, smem, grid, wpb, st))) return rc;
   } else {
+  a.flat = group == 1 ? 1u : 0u;
   size_t smem = search_layout(a, nw);
   if (smem > 200 * 1024)
     return fail(SEISMIC_EBUDGET, "search: shared memory per query (" + std::to_string(smem) +

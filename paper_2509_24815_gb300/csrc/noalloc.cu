@@ -122,6 +122,7 @@ extern "C" int seismic_search_noalloc(seismic_index *ix, const seismic_csr *quer
   a.sum_absmax = ix->sum_absmax;
   a.prefetch = p->no_prefetch ? 0u : 256u;
   a.perm = nullptr;
+  a.flat = group == 1 ? 1u : 0u;
   const size_t smem = search_layout(a, nw);
   if (smem > 200 * 1024) return fail(SEISMIC_EBUDGET, "search: shared memory per query exceeds 200 KB");
   int blocks = 1;

@@ -94,22 +94,39 @@ __device__ uint32_t block_rank_scan(const uint32_t *bits, uint16_t *rank, uint32
   return total;
 }
 
+// The query's shared-memory arrays.  Each is addressed from the dynamic
+// shared-memory base and its offset in the launch arguments (constant bank)
+// when used, so no pointer to them stays live in a register.
+extern __shared__ __align__(16) unsigned char g_sm[];
+
 struct Smem {
-  uint32_t *qbits;
-  uint16_t *qrank;
-  float *qval;
-  uint16_t *qterm;
-  uint16_t *cutT;
-  float *aq;
-  float *part;
-  unsigned long long *keys;
-  uint32_t *clo, *chi;
-  uint32_t *hash;
+  const SearchArgs &a;
   uint32_t *seen;  // this CTA's global bitmap, or NULL
-  float *tk_s, *tmp_s, *cand_s;
-  uint32_t *tk_id, *tmp_id, *cand_id;
-  uint8_t *cand_ok;
-  uint32_t *woff, *wstart;  // the current wave's blocks
+  __device__ __forceinline__ uint32_t *qbits() const { return reinterpret_cast<uint32_t *>(g_sm + a.off_qbits); }
+  __device__ __forceinline__ uint16_t *qrank() const { return reinterpret_cast<uint16_t *>(g_sm + a.off_qrank); }
+  __device__ __forceinline__ float *qval() const { return reinterpret_cast<float *>(g_sm + a.off_qval); }
+  __device__ __forceinline__ uint16_t *qterm() const { return reinterpret_cast<uint16_t *>(g_sm + a.off_qterm); }
+  __device__ __forceinline__ uint16_t *cutT() const { return reinterpret_cast<uint16_t *>(g_sm + a.off_cut); }
+  __device__ __forceinline__ float *aq() const { return reinterpret_cast<float *>(g_sm + a.off_aq); }
+  __device__ __forceinline__ float *part() const { return reinterpret_cast<float *>(g_sm + a.off_part); }
+  __device__ __forceinline__ unsigned long long *keys() const { return reinterpret_cast<unsigned long long *>(g_sm + a.off_keys); }
+  __device__ __forceinline__ uint32_t *clo() const { return reinterpret_cast<uint32_t *>(g_sm + a.off_clo); }
+  __device__ __forceinline__ uint32_t *chi() const { return reinterpret_cast<uint32_t *>(g_sm + a.off_chi); }
+  __device__ __forceinline__ uint32_t *hash() const { return reinterpret_cast<uint32_t *>(g_sm + a.off_hash); }
+  __device__ __forceinline__ float *tk_s() const { return reinterpret_cast<float *>(g_sm + a.off_tk_s); }
+  __device__ __forceinline__ float *tmp_s() const { return reinterpret_cast<float *>(g_sm + a.off_tmp_s); }
+  __device__ __forceinline__ float *cand_s() const { return reinterpret_cast<float *>(g_sm + a.off_cand_s); }
+  __device__ __forceinline__ uint32_t *tk_id() const { return reinterpret_cast<uint32_t *>(g_sm + a.off_tk_id); }
+  __device__ __forceinline__ uint32_t *tmp_id() const { return reinterpret_cast<uint32_t *>(g_sm + a.off_tmp_id); }
+  __device__ __forceinline__ uint32_t *cand_id() const { return reinterpret_cast<uint32_t *>(g_sm + a.off_cand_id); }
+  __device__ __forceinline__ uint8_t *cand_ok() const { return reinterpret_cast<uint8_t *>(g_sm + a.off_cand_ok); }
+  __device__ __forceinline__ uint32_t *woff() const { return reinterpret_cast<uint32_t *>(g_sm + a.off_wave); }
+  __device__ __forceinline__ uint32_t *bptr() const { return reinterpret_cast<uint32_t *>(g_sm + a.off_bptr); }
+  __device__ __forceinline__ uint32_t *fdoc() const { return reinterpret_cast<uint32_t *>(g_sm + a.off_fdoc); }
+  __device__ __forceinline__ uint32_t *fc0() const { return reinterpret_cast<uint32_t *>(g_sm + a.off_fc0); }
+  __device__ __forceinline__ uint32_t *fpre() const { return reinterpret_cast<uint32_t *>(g_sm + a.off_fpre); }
+  __device__ __forceinline__ uint8_t *cmap() const { return reinterpret_cast<uint8_t *>(g_sm + a.off_cmap); }
+  __device__ __forceinline__ uint32_t *wstart() const { return woff() + (kMaxWave + 1); }
 };
 
 struct Shared {
@@ -127,42 +144,42 @@ __device__ void merge_candidates(const SearchArgs &a, Smem &s, Shared &sh) {
   if (m == 0) return;  // uniform: every thread read the same ncand after the barrier
   const bool dupcheck = sh.hash_full != 0u;
   for (uint32_t i = tid; i < m; i += NT) {
-    const uint32_t id = s.cand_id[i];
+    const uint32_t id = s.cand_id()[i];
     uint8_t ok = 1;
     for (uint32_t j = 0; j < cnt; j++)
-      if (s.tk_id[j] == id) { ok = 0; break; }
+      if (s.tk_id()[j] == id) { ok = 0; break; }
     if (ok && dupcheck)
       for (uint32_t j = 0; j < i; j++)
-        if (s.cand_id[j] == id) { ok = 0; break; }
-    s.cand_ok[i] = ok;
+        if (s.cand_id()[j] == id) { ok = 0; break; }
+    s.cand_ok()[i] = ok;
     if (ok) atomicAdd(&sh.nvalid, 1u);
   }
   __syncthreads();
   for (uint32_t i = tid; i < m; i += NT) {
-    if (!s.cand_ok[i]) continue;
-    const float sc = s.cand_s[i];
-    const uint32_t id = s.cand_id[i];
+    if (!s.cand_ok()[i]) continue;
+    const float sc = s.cand_s()[i];
+    const uint32_t id = s.cand_id()[i];
     uint32_t lo = 0, hi = cnt;  // topk entries better than (sc, id)
     while (lo < hi) {
       uint32_t mid = (lo + hi) >> 1;
-      if (better(s.tk_s[mid], s.tk_id[mid], sc, id)) lo = mid + 1; else hi = mid;
+      if (better(s.tk_s()[mid], s.tk_id()[mid], sc, id)) lo = mid + 1; else hi = mid;
     }
     uint32_t r = lo;
     for (uint32_t j = 0; j < m; j++)
-      if (s.cand_ok[j] && better(s.cand_s[j], s.cand_id[j], sc, id)) r++;
-    if (r < k) { s.tmp_s[r] = sc; s.tmp_id[r] = id; }
+      if (s.cand_ok()[j] && better(s.cand_s()[j], s.cand_id()[j], sc, id)) r++;
+    if (r < k) { s.tmp_s()[r] = sc; s.tmp_id()[r] = id; }
   }
   for (uint32_t i = tid; i < cnt; i += NT) {
-    const float sc = s.tk_s[i];
-    const uint32_t id = s.tk_id[i];
+    const float sc = s.tk_s()[i];
+    const uint32_t id = s.tk_id()[i];
     uint32_t r = i;
     for (uint32_t j = 0; j < m; j++)
-      if (s.cand_ok[j] && better(s.cand_s[j], s.cand_id[j], sc, id)) r++;
-    if (r < k) { s.tmp_s[r] = sc; s.tmp_id[r] = id; }
+      if (s.cand_ok()[j] && better(s.cand_s()[j], s.cand_id()[j], sc, id)) r++;
+    if (r < k) { s.tmp_s()[r] = sc; s.tmp_id()[r] = id; }
   }
   __syncthreads();
   const uint32_t nc = min(k, cnt + sh.nvalid);
-  for (uint32_t i = tid; i < nc; i += NT) { s.tk_s[i] = s.tmp_s[i]; s.tk_id[i] = s.tmp_id[i]; }
+  for (uint32_t i = tid; i < nc; i += NT) { s.tk_s()[i] = s.tmp_s()[i]; s.tk_id()[i] = s.tmp_id()[i]; }
   __syncthreads();
   if (tid == 0) { sh.count = nc; sh.ncand = 0; sh.nvalid = 0; }
   __syncthreads();
@@ -176,12 +193,14 @@ __device__ void eval_wave(const SearchArgs &a, Smem &s, Shared &sh, uint32_t n, 
   const uint32_t lane = tid & 31;
   const uint32_t gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(uint32_t)(G - 1)));
   const bool full = sh.count == a.k;
-  const float th = full ? s.tk_s[a.k - 1] : -INFINITY;
-  const uint32_t thid = full ? s.tk_id[a.k - 1] : 0u;
+  const float th = full ? s.tk_s()[a.k - 1] : -INFINITY;
+  const uint32_t thid = full ? s.tk_id()[a.k - 1] : 0u;
   if (a.prefetch && n > (uint32_t)NG) {  // every row of the wave into L2, one bulk prefetch each
     for (uint32_t i = tid; i < n; i += NT) {
-      const uint32_t d = src.id(i);
-      if (d != SEISMIC_NONE_ID) prefetch_row(a.fwd_data, src.row(i, d));
+      uint32_t d;
+      unsigned long long row;
+      src.fetch(i, d, row);
+      if (d != SEISMIC_NONE_ID) prefetch_row(a.fwd_data, row);
     }
   }
   // Software pipeline per lane group: the next document's (id, row) are loaded
@@ -189,26 +208,20 @@ __device__ void eval_wave(const SearchArgs &a, Smem &s, Shared &sh, uint32_t n, 
   // the row's loads and read after the dot (a seen document's score is dropped).
   uint32_t dn = SEISMIC_NONE_ID;
   unsigned long long rn = 0ull;
-  if ((uint32_t)grp < n) {
-    dn = src.id(grp);
-    rn = src.row(grp, dn);
-  }
+  if ((uint32_t)grp < n) src.fetch(grp, dn, rn);
   for (uint32_t i = grp; i < n; i += NG) {
     const uint32_t d = dn;
     const unsigned long long row = rn;
-    if (i + NG < n) {
-      dn = src.id(i + NG);
-      rn = src.row(i + NG, dn);
-    }
+    if (i + NG < n) src.fetch(i + NG, dn, rn);
     if (d == SEISMIC_NONE_ID) continue;
     uint32_t old = 0u, fresh = 0u;
     const uint32_t bit = 1u << (d & 31);
     if (gl == 0) {
       if (s.seen) old = atomicOr(s.seen + (d >> 5), bit);
-      else fresh = seen_insert(s.hash, a.HS - 1u, d, &sh.hash_full) ? 1u : 0u;
+      else fresh = seen_insert(s.hash(), a.HS - 1u, d, &sh.hash_full) ? 1u : 0u;
     }
-    const float p = row_dot<G>(a.fwd_data, (uint32_t)row, (uint32_t)(row >> 32), gl, gmask, s.qbits, s.qrank,
-                               s.qval);
+    const float p = row_dot<G>(a.fwd_data, (uint32_t)row, (uint32_t)(row >> 32), gl, gmask, s.qbits(), s.qrank(),
+                               s.qval());
     if (s.seen) fresh = (old & bit) ? 0u : 1u;
     fresh = __shfl_sync(gmask, fresh, 0, G);
     if (!fresh) continue;
@@ -219,13 +232,172 @@ __device__ void eval_wave(const SearchArgs &a, Smem &s, Shared &sh, uint32_t n, 
       }
       if (!full || better(p, d, th, thid)) {
         uint32_t pos = atomicAdd(&sh.ncand, 1u);
-        s.cand_s[pos] = p;
-        s.cand_id[pos] = d;
+        s.cand_s()[pos] = p;
+        s.cand_id()[pos] = d;
       }
     }
   }
   __syncthreads();
   merge_candidates<NT>(a, s, sh);
+}
+
+// v[0..n) -> exclusive prefix sums, v[n] = the total (n <= 32 * NT).  Starts
+// and ends with a barrier-separated phase; every thread must call it.
+template <int NT>
+__device__ uint32_t block_exclusive_scan(uint32_t *v, uint32_t n, uint32_t *wtmp) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int nw = NT / 32;
+  const uint32_t per = (n + NT - 1) / NT, lo = min(n, tid * per), hi = min(n, lo + per);
+  uint32_t sum = 0;
+  for (uint32_t i = lo; i < hi; i++) sum += v[i];
+  uint32_t x = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wtmp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < nw ? wtmp[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < nw) wtmp[lane] = w;
+  }
+  __syncthreads();
+  uint32_t run = (warp ? wtmp[warp - 1] : 0) + x - sum;
+  for (uint32_t i = lo; i < hi; i++) {
+    const uint32_t c = v[i];
+    v[i] = run;
+    run += c;
+  }
+  const uint32_t total = wtmp[nw - 1];
+  if (tid == 0) v[n] = total;
+  __syncthreads();
+  return total;
+}
+
+// Group 1: the wave's documents are deduplicated first (one thread each),
+// then their rows' chunks are laid end to end and scored by all threads of
+// the CTA, U chunks in flight per thread, each chunk's 8 products added in
+// entry order; a document's score is the sum of its chunks' partials in chunk
+// order (deterministic, independent of the launch shape).  Work per thread is
+// balanced whatever the row lengths; seen documents cost no row reads.
+template <int NT, class Src>
+__device__ __forceinline__ void eval_wave_flat(const SearchArgs &a, Smem &s, Shared &sh, uint32_t n, const Src &src,
+                                               int knn_stage) {
+  constexpr int U = 2;
+  const int tid = threadIdx.x;
+  const bool full = sh.count == a.k;
+  const float th = full ? s.tk_s()[a.k - 1] : -INFINITY;
+  const uint32_t thid = full ? s.tk_id()[a.k - 1] : 0u;
+  float *cpart = s.part();  // the block-score partials are dead while documents are scored
+  for (uint32_t i = tid; i < n; i += NT) {
+    uint32_t d;
+    unsigned long long row;
+    src.fetch(i, d, row);
+    uint32_t keep = SEISMIC_NONE_ID, nch = 0;
+    if (d != SEISMIC_NONE_ID) {
+      bool fresh;
+      if (s.seen) {
+        const uint32_t bit = 1u << (d & 31);
+        fresh = !(atomicOr(s.seen + (d >> 5), bit) & bit);
+      } else {
+        fresh = seen_insert(s.hash(), a.HS - 1u, d, &sh.hash_full);
+      }
+      if (fresh) {
+        keep = d;
+        nch = (uint32_t)(row >> 32);
+        if (a.prefetch) prefetch_row(a.fwd_data, row);
+        if (a.stats) {
+          atomicAdd(&sh.st[knn_stage ? SEISMIC_ST_KNN_DOCS : SEISMIC_ST_DOCS], 1ull);
+          atomicAdd(&sh.st[knn_stage ? SEISMIC_ST_KNN_NNZ : SEISMIC_ST_DOC_NNZ], (unsigned long long)a.fwd_nnz[d]);
+        }
+      }
+    }
+    s.fdoc()[i] = keep;
+    s.fc0()[i] = (uint32_t)row;
+    s.fpre()[i] = nch;
+  }
+  __syncthreads();
+  block_exclusive_scan<NT>(s.fpre(), n, sh.wtmp);
+  const uint32_t *qb = s.qbits();
+  const uint16_t *qr = s.qrank();
+  const float *qv = s.qval();
+  uint32_t i0 = 0;
+  while (i0 < n) {
+    // a pass: the documents from i0 whose chunks fit in CAPC (one always does)
+    const uint32_t base = s.fpre()[i0];
+    uint32_t lo = i0 + 1, hi = n;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1;
+      if (s.fpre()[mid] - base <= a.CAPC) lo = mid; else hi = mid - 1;
+    }
+    const uint32_t i1 = lo, total = s.fpre()[i1] - base;
+    for (uint32_t i = i0 + tid; i < i1; i += NT) {
+      const uint32_t e = s.fpre()[i + 1] - base;
+      for (uint32_t c = s.fpre()[i] - base; c < e; c++) s.cmap()[c] = (uint8_t)i;  // i < CAND <= 256
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (uint32_t j = tid; j < total; j += NT * U) {
+      uint4 t[U], va[U], vb[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {  // past the end: the last chunk again (unconditional loads stay in registers)
+        const uint32_t jj = min(j + u * NT, total - 1u);
+        {  // a row holds its chunks' terms (16 B each), then their values (32 B each)
+          const uint32_t i = s.cmap()[jj], p0 = s.fpre()[i];
+          const uint32_t nch = s.fpre()[i + 1] - p0, o = base + jj - p0;
+          const uint8_t *row = a.fwd_data + (size_t)s.fc0()[i] * 48;
+          t[u] = ldg_na(row + 16 * o);
+          va[u] = ldg_na(row + 16 * nch + 32 * o);
+          vb[u] = ldg_na(row + 16 * nch + 32 * o + 16);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const uint32_t jj = j + u * NT;
+        if (jj < total) {
+          const uint32_t tw[4] = {t[u].x, t[u].y, t[u].z, t[u].w};
+          const uint32_t vv[8] = {va[u].x, va[u].y, va[u].z, va[u].w, vb[u].x, vb[u].y, vb[u].z, vb[u].w};
+          float acc = 0.0f;
+#pragma unroll
+          for (int e = 0; e < 8; e++) {  // absent terms (most) cost one shared load
+            const uint32_t tt = (e & 1) ? (tw[e >> 1] >> 16) : (tw[e >> 1] & 0xFFFFu);
+            const uint32_t w = qb[tt >> 5], sh5 = tt & 31u;
+            if ((w >> sh5) & 1u) acc = fmaf(qv[qr[tt >> 5] + __popc(w & ((1u << sh5) - 1u))], __uint_as_float(vv[e]), acc);
+          }
+          cpart[jj] = acc;
+        }
+      }
+    }
+    __syncthreads();
+    for (uint32_t i = i0 + tid; i < i1; i += NT) {
+      const uint32_t d = s.fdoc()[i];
+      if (d == SEISMIC_NONE_ID) continue;
+      const uint32_t e = s.fpre()[i + 1] - base;
+      float p = 0.0f;
+      for (uint32_t c = s.fpre()[i] - base; c < e; c++) p += cpart[c];
+      if (!full || better(p, d, th, thid)) {
+        const uint32_t pos = atomicAdd(&sh.ncand, 1u);
+        s.cand_s()[pos] = p;
+        s.cand_id()[pos] = d;
+      }
+    }
+    __syncthreads();
+    i0 = i1;
+  }
+  merge_candidates<NT>(a, s, sh);
+}
+
+template <int G, int NT, class Src>
+__device__ __forceinline__ void eval(const SearchArgs &a, Smem &s, Shared &sh, uint32_t n, const Src &src,
+                                     int knn_stage) {
+  if constexpr (G == 1) eval_wave_flat<NT>(a, s, sh, n, src, knn_stage);
+  else eval_wave<G, NT>(a, s, sh, n, src, knn_stage);
 }
 
 template <int NT>
@@ -245,33 +417,13 @@ __device__ void bitonic_sort_u64(unsigned long long *keys, uint32_t P2) {
     }
 }
 
+// 5 CTAs of 256 threads per SM (48 registers)
 template <int G, int NW>
-__global__ void __launch_bounds__(NW * 32, 1280 / (NW * 32)) k_search(const SearchArgs a) {
+__global__ void __launch_bounds__(NW * 32, 1280 / (NW * 32))
+    k_search(const __grid_constant__ SearchArgs a) {
   constexpr int NT = NW * 32;
-  extern __shared__ __align__(16) unsigned char sm[];
   __shared__ Shared sh;
-  Smem s;
-  s.qbits = reinterpret_cast<uint32_t *>(sm + a.off_qbits);
-  s.qrank = reinterpret_cast<uint16_t *>(sm + a.off_qrank);
-  s.qval = reinterpret_cast<float *>(sm + a.off_qval);
-  s.qterm = reinterpret_cast<uint16_t *>(sm + a.off_qterm);
-  s.cutT = reinterpret_cast<uint16_t *>(sm + a.off_cut);
-  s.aq = reinterpret_cast<float *>(sm + a.off_aq);
-  s.part = reinterpret_cast<float *>(sm + a.off_part);
-  s.keys = reinterpret_cast<unsigned long long *>(sm + a.off_keys);
-  s.clo = reinterpret_cast<uint32_t *>(sm + a.off_clo);
-  s.chi = reinterpret_cast<uint32_t *>(sm + a.off_chi);
-  s.hash = reinterpret_cast<uint32_t *>(sm + a.off_hash);
-  s.tk_s = reinterpret_cast<float *>(sm + a.off_tk_s);
-  s.tk_id = reinterpret_cast<uint32_t *>(sm + a.off_tk_id);
-  s.tmp_s = reinterpret_cast<float *>(sm + a.off_tmp_s);
-  s.tmp_id = reinterpret_cast<uint32_t *>(sm + a.off_tmp_id);
-  s.cand_s = reinterpret_cast<float *>(sm + a.off_cand_s);
-  s.cand_id = reinterpret_cast<uint32_t *>(sm + a.off_cand_id);
-  s.cand_ok = reinterpret_cast<uint8_t *>(sm + a.off_cand_ok);
-  s.woff = reinterpret_cast<uint32_t *>(sm + a.off_wave);
-  s.wstart = s.woff + (kMaxWave + 1);
-  s.seen = a.seen_bm ? a.seen_bm + (size_t)blockIdx.x * a.seen_words : nullptr;
+  Smem s{a, a.seen_bm ? a.seen_bm + (size_t)blockIdx.x * a.seen_words : nullptr};
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   bool first = true;
 
@@ -291,12 +443,12 @@ __global__ void __launch_bounds__(NW * 32, 1280 / (NW * 32)) k_search(const Sear
     // ---------------------------------------------------------- H0: ingest
     const uint64_t qb = a.q_indptr[q], qe = a.q_indptr[q + 1];
     const uint32_t nnz = (uint32_t)(qe - qb);
-    for (uint32_t i = tid; i < a.W; i += NT) s.qbits[i] = 0u;
+    for (uint32_t i = tid; i < a.W; i += NT) s.qbits()[i] = 0u;
     if (s.seen) {  // seen_words is a multiple of 4 and the slot is 16-byte aligned
       uint4 *z = reinterpret_cast<uint4 *>(s.seen);
       for (uint32_t i = tid; i < a.seen_words / 4; i += NT) z[i] = make_uint4(0u, 0u, 0u, 0u);
     } else {
-      for (uint32_t i = tid; i < a.HS; i += NT) s.hash[i] = 0u;
+      for (uint32_t i = tid; i < a.HS; i += NT) s.hash()[i] = 0u;
     }
     if (tid < SEISMIC_STATS_N) sh.st[tid] = 0ull;
     if (tid == 0) {
@@ -313,12 +465,12 @@ __global__ void __launch_bounds__(NW * 32, 1280 / (NW * 32)) k_search(const Sear
       const float v = a.q_vals[qb + i];
       if (v != 0.0f) {
         const uint32_t t = a.q_terms[qb + i];
-        if (t < a.dim) atomicOr(&s.qbits[t >> 5], 1u << (t & 31));
+        if (t < a.dim) atomicOr(&s.qbits()[t >> 5], 1u << (t & 31));
         else sh.bad = 1u;
       }
     }
     __syncthreads();
-    const uint32_t nzq = block_rank_scan<NT>(s.qbits, s.qrank, a.W, sh.wtmp);
+    const uint32_t nzq = block_rank_scan<NT>(s.qbits(), s.qrank(), a.W, sh.wtmp);
     if (nzq > a.QN || sh.bad) {  // more nonzeros than the launch was sized for, or a bad term
       if (tid == 0) atomicOr(a.queue + 1, 1u);
       for (uint32_t i = tid; i < a.k; i += NT) {
@@ -333,10 +485,10 @@ __global__ void __launch_bounds__(NW * 32, 1280 / (NW * 32)) k_search(const Sear
       const float v = a.q_vals[qb + i];
       if (v != 0.0f) {
         const uint32_t t = a.q_terms[qb + i];
-        const uint32_t w = s.qbits[t >> 5];
-        const uint32_t pos = s.qrank[t >> 5] + __popc(w & ((1u << (t & 31)) - 1u));
-        s.qval[pos] = v;
-        s.qterm[pos] = (uint16_t)t;
+        const uint32_t w = s.qbits()[t >> 5];
+        const uint32_t pos = s.qrank()[t >> 5] + __popc(w & ((1u << (t & 31)) - 1u));
+        s.qval()[pos] = v;
+        s.qterm()[pos] = (uint16_t)t;
       }
     }
     __syncthreads();
@@ -344,25 +496,25 @@ __global__ void __launch_bounds__(NW * 32, 1280 / (NW * 32)) k_search(const Sear
     // ---------------------------------------------------------- H1: list terms
     if (a.alpha_q > 0.0f) {
       for (uint32_t i = tid; i < nzq; i += NT) {
-        const float av = fabsf(s.qval[i]);
-        const uint32_t t = s.qterm[i];
+        const float av = fabsf(s.qval()[i]);
+        const uint32_t t = s.qterm()[i];
         uint32_t r = 0;
         for (uint32_t j = 0; j < nzq; j++) {
-          const float aj = fabsf(s.qval[j]);
-          r += (aj > av || (aj == av && s.qterm[j] < t)) ? 1u : 0u;
+          const float aj = fabsf(s.qval()[j]);
+          r += (aj > av || (aj == av && s.qterm()[j] < t)) ? 1u : 0u;
         }
-        s.aq[r] = av;
-        s.cutT[r] = (uint16_t)t;
+        s.aq()[r] = av;
+        s.cutT()[r] = (uint16_t)t;
       }
       __syncthreads();
       if (tid == 0) {  // alpha_q-MSS: fp64 prefix mass in sketch order
         double tot = 0.0;
-        for (uint32_t i = 0; i < nzq; i++) tot += (double)s.aq[i];
+        for (uint32_t i = 0; i < nzq; i++) tot += (double)s.aq()[i];
         const double target = (double)a.alpha_q * tot;
         double c = 0.0;
         uint32_t keep = nzq;
         for (uint32_t i = 0; i < nzq; i++) {
-          c += (double)s.aq[i];
+          c += (double)s.aq()[i];
           if (c >= target) { keep = i + 1; break; }
         }
         sh.ncut = keep;
@@ -370,14 +522,14 @@ __global__ void __launch_bounds__(NW * 32, 1280 / (NW * 32)) k_search(const Sear
     } else {
       const uint32_t cut = sh.cut;
       for (uint32_t i = tid; i < nzq; i += NT) {
-        const float v = s.qval[i];
-        const uint32_t t = s.qterm[i];
+        const float v = s.qval()[i];
+        const uint32_t t = s.qterm()[i];
         uint32_t r = 0;
         for (uint32_t j = 0; j < nzq; j++) {
-          const float vj = s.qval[j];
-          r += (vj > v || (vj == v && s.qterm[j] < t)) ? 1u : 0u;
+          const float vj = s.qval()[j];
+          r += (vj > v || (vj == v && s.qterm()[j] < t)) ? 1u : 0u;
         }
-        if (r < cut) s.cutT[r] = (uint16_t)t;
+        if (r < cut) s.cutT()[r] = (uint16_t)t;
       }
       if (tid == 0) sh.ncut = min(cut, nzq);
     }
@@ -388,7 +540,7 @@ __global__ void __launch_bounds__(NW * 32, 1280 / (NW * 32)) k_search(const Sear
 
     // ---------------------------------------------------------- lists
     for (uint32_t li = 0; li < ncut; li++) {
-      const uint32_t t = s.cutT[li];
+      const uint32_t t = s.cutT()[li];
       const uint32_t g0 = a.blk_ptr[t], nb = a.blk_ptr[t + 1] - g0;
       if (a.stats && tid == 0) sh.st[SEISMIC_ST_LISTS]++;
       if (nb == 0) continue;
@@ -401,27 +553,28 @@ __global__ void __launch_bounds__(NW * 32, 1280 / (NW * 32)) k_search(const Sear
         for (uint32_t c0 = d0; c0 < d1; c0 += a.CAND) {
           const uint32_t n = min(a.CAND, d1 - c0);
           const MemberSrc src{a.bdoc + c0, a.bdoc_row + c0};
-          eval_wave<G, NT>(a, s, sh, n, src, 0);
+          eval<G, NT>(a, s, sh, n, src, 0);
         }
         continue;
       }
       // ---- H2: summary scores of every block of the list
       const size_t dbase = (size_t)t * (a.dim + 1u);
       for (uint32_t i = tid; i < nzq; i += NT) {
-        const uint32_t sterm = s.qterm[i];
-        s.clo[i] = __ldg(a.sdir + dbase + sterm);
-        s.chi[i] = __ldg(a.sdir + dbase + sterm + 1);
+        const uint32_t sterm = s.qterm()[i];
+        s.clo()[i] = __ldg(a.sdir + dbase + sterm);
+        s.chi()[i] = __ldg(a.sdir + dbase + sterm + 1);
       }
-      for (uint32_t i = tid; i < NW * a.BMAX; i += NT) s.part[i] = 0.0f;
+      for (uint32_t i = tid; i < NW * a.BMAX; i += NT) s.part()[i] = 0.0f;
+      for (uint32_t b = tid; b <= nb; b += NT) s.bptr()[b] = __ldg(a.bdoc_ptr + g0 + b);  // block member ranges
       __syncthreads();
       {
-        float *pw = s.part + warp * a.BMAX;
+        float *pw = s.part() + warp * a.BMAX;
         const float *bm = a.blk_m + g0;
         const float *bs = a.blk_size + g0;
         uint32_t ent = 0;
         for (uint32_t i = warp; i < nzq; i += NW) {
-          const uint32_t lo = s.clo[i], hi = s.chi[i];
-          const float qv = s.qval[i];
+          const uint32_t lo = s.clo()[i], hi = s.chi()[i];
+          const float qv = s.qval()[i];
           ent += hi - lo;
           for (uint32_t e = lo + lane; e < hi; e += 32) {
             const uint32_t b = __ldg(a.scol_blk + e);
@@ -440,10 +593,10 @@ __global__ void __launch_bounds__(NW * 32, 1280 / (NW * 32)) k_search(const Sear
       for (uint32_t b = tid; b < P2; b += NT) {
         if (b < nb) {
           float r = 0.0f;
-          for (int w = 0; w < NW; w++) r += s.part[w * a.BMAX + b];
-          s.keys[b] = ((unsigned long long)(~f2ord(r)) << 32) | b;
+          for (int w = 0; w < NW; w++) r += s.part()[w * a.BMAX + b];
+          s.keys()[b] = ((unsigned long long)(~f2ord(r)) << 32) | b;
         } else {
-          s.keys[b] = ~0ull;
+          s.keys()[b] = ~0ull;
         }
       }
       if (a.stats && tid == 0) {
@@ -452,16 +605,16 @@ __global__ void __launch_bounds__(NW * 32, 1280 / (NW * 32)) k_search(const Sear
       }
       __syncthreads();
       // ---- H3: order blocks by (r desc, block asc)
-      bitonic_sort_u64<NT>(s.keys, P2);
+      bitonic_sort_u64<NT>(s.keys(), P2);
       // ---- H4/H5/H6: visit blocks in order, waves of a.wave blocks
       const uint32_t W = min(a.wave, kMaxWave);
       uint32_t bi = 0;
       while (bi < nb) {
         // skip test at the head of the wave (uniform: shared state after a barrier)
         const bool fullk = sh.count == a.k;
-        const float theta = fullk ? s.tk_s[a.k - 1] : -INFINITY;
+        const float theta = fullk ? s.tk_s()[a.k - 1] : -INFINITY;
         const float thr = a.hf_mode == 0 ? hf * theta : theta / hf;
-        if (fullk && ord2f(~(uint32_t)(s.keys[bi] >> 32)) < thr) {
+        if (fullk && ord2f(~(uint32_t)(s.keys()[bi] >> 32)) < thr) {
           if (a.stats && tid == 0) sh.st[SEISMIC_ST_BLOCKS_SKIPPED] += nb - bi;
           break;
         }
@@ -469,16 +622,16 @@ __global__ void __launch_bounds__(NW * 32, 1280 / (NW * 32)) k_search(const Sear
         // W blocks and CAND documents (a larger block goes alone, in pieces)
         uint32_t be = bi, ndocs = 0;
         while (be < nb && be - bi < W) {
-          const uint32_t b = (uint32_t)(s.keys[be] & 0xFFFFFFFFu);
-          if (be > bi && fullk && ord2f(~(uint32_t)(s.keys[be] >> 32)) < thr) break;
-          const uint32_t nd = a.bdoc_ptr[g0 + b + 1] - a.bdoc_ptr[g0 + b];
+          const uint32_t b = (uint32_t)(s.keys()[be] & 0xFFFFFFFFu);
+          if (be > bi && fullk && ord2f(~(uint32_t)(s.keys()[be] >> 32)) < thr) break;
+          const uint32_t nd = s.bptr()[b + 1] - s.bptr()[b];
           if (be > bi && ndocs + nd > a.CAND) break;
           ndocs += nd;
           be++;
         }
         if (a.prefetch && tid < W && be + tid < nb) {  // member lists of the next wave's blocks
-          const uint32_t b = (uint32_t)(s.keys[be + tid] & 0xFFFFFFFFu);
-          const uint32_t e0 = __ldg(a.bdoc_ptr + g0 + b), e1 = __ldg(a.bdoc_ptr + g0 + b + 1);
+          const uint32_t b = (uint32_t)(s.keys()[be + tid] & 0xFFFFFFFFu);
+          const uint32_t e0 = s.bptr()[b], e1 = s.bptr()[b + 1];
           prefetch_l2(a.bdoc + e0, 4 * (e1 - e0));
           prefetch_l2(a.bdoc_row + e0, 8 * (e1 - e0));
         }
@@ -487,30 +640,26 @@ __global__ void __launch_bounds__(NW * 32, 1280 / (NW * 32)) k_search(const Sear
           sh.st[SEISMIC_ST_BLOCK_DOCS] += ndocs;
         }
         if (be - bi == 1) {
-          const uint32_t b = (uint32_t)(s.keys[bi] & 0xFFFFFFFFu);
-          const uint32_t d0 = a.bdoc_ptr[g0 + b], d1 = a.bdoc_ptr[g0 + b + 1];
+          const uint32_t b = (uint32_t)(s.keys()[bi] & 0xFFFFFFFFu);
+          const uint32_t d0 = s.bptr()[b], d1 = s.bptr()[b + 1];
           for (uint32_t c0 = d0; c0 < d1; c0 += a.CAND) {
             const MemberSrc src{a.bdoc + c0, a.bdoc_row + c0};
-            eval_wave<G, NT>(a, s, sh, min(a.CAND, d1 - c0), src, 0);
+            eval<G, NT>(a, s, sh, min(a.CAND, d1 - c0), src, 0);
           }
         } else {
-          if (tid < be - bi) {
-            const uint32_t b = (uint32_t)(s.keys[bi + tid] & 0xFFFFFFFFu);
-            s.wstart[tid] = a.bdoc_ptr[g0 + b];
-          }
-          __syncthreads();
           if (tid == 0) {
             uint32_t acc = 0;
             for (uint32_t w = 0; w < be - bi; w++) {
-              s.woff[w] = acc;
-              const uint32_t b = (uint32_t)(s.keys[bi + w] & 0xFFFFFFFFu);
-              acc += a.bdoc_ptr[g0 + b + 1] - s.wstart[w];
+              const uint32_t b = (uint32_t)(s.keys()[bi + w] & 0xFFFFFFFFu);
+              s.woff()[w] = acc;
+              s.wstart()[w] = s.bptr()[b];
+              acc += s.bptr()[b + 1] - s.bptr()[b];
             }
-            s.woff[be - bi] = acc;
+            s.woff()[be - bi] = acc;
           }
           __syncthreads();
-          const WaveSrc src{s.woff, s.wstart, be - bi, a.bdoc, a.bdoc_row};
-          eval_wave<G, NT>(a, s, sh, ndocs, src, 0);
+          const WaveSrc src{s.woff(), s.wstart(), be - bi, a.bdoc, a.bdoc_row};
+          eval<G, NT>(a, s, sh, ndocs, src, 0);
         }
         bi = be;
       }
@@ -520,28 +669,29 @@ __global__ void __launch_bounds__(NW * 32, 1280 / (NW * 32)) k_search(const Sear
     // ---------------------------------------------------------- H7: kappa-NN expansion
     if (a.use_knn && a.kappa > 0 && sh.count > 0) {
       const uint32_t ns = sh.count;
-      for (uint32_t i = tid; i < ns; i += NT) s.clo[i] = s.tk_id[i];  // S, fixed before expanding
+      for (uint32_t i = tid; i < ns; i += NT) s.clo()[i] = s.tk_id()[i];  // S, fixed before expanding
       __syncthreads();
       const uint32_t total = ns * a.kappa;
       for (uint32_t c0 = 0; c0 < total; c0 += a.CAND) {
         const uint32_t n = min(a.CAND, total - c0);
-        const GraphSrc src{s.clo, a.knn + (size_t)0, a.fwd_cptr, a.kappa};
+        const GraphSrc src{s.clo(), a.knn + (size_t)0, a.fwd_cptr, a.kappa};
         // positions c0 .. c0 + n of the neighbour list of S
         struct Shifted {
           GraphSrc g;
           uint32_t c0;
           __device__ uint32_t id(uint32_t i) const { return g.id(c0 + i); }
           __device__ unsigned long long row(uint32_t i, uint32_t d) const { return g.row(c0 + i, d); }
+          __device__ void fetch(uint32_t i, uint32_t &d, unsigned long long &r) const { g.fetch(c0 + i, d, r); }
         } sh_src{src, c0};
-        eval_wave<G, NT>(a, s, sh, n, sh_src, 1);
+        eval<G, NT>(a, s, sh, n, sh_src, 1);
       }
     }
 
     // ---------------------------------------------------------- output
     for (uint32_t i = tid; i < a.k; i += NT) {
       const bool ok = i < sh.count;
-      a.ids[(size_t)q * a.k + i] = ok ? s.tk_id[i] : SEISMIC_NONE_ID;
-      a.scores[(size_t)q * a.k + i] = ok ? s.tk_s[i] : -INFINITY;
+      a.ids[(size_t)q * a.k + i] = ok ? s.tk_id()[i] : SEISMIC_NONE_ID;
+      a.scores[(size_t)q * a.k + i] = ok ? s.tk_s()[i] : -INFINITY;
     }
     if (a.stats && tid < SEISMIC_STATS_N) a.stats[(size_t)q * SEISMIC_STATS_N + tid] = sh.st[tid];
     __syncthreads();
@@ -599,27 +749,43 @@ size_t search_layout(SearchArgs &a, uint32_t nw) {
   a.off_cand_id = take(a.CAND * 4);
   a.off_cand_ok = take(a.CAND);
   a.off_wave = take(2 * (kMaxWave + 1) * 4);
+  a.off_bptr = take(a.exhaustive ? 4 : (a.BMAX + 1) * 4);
+  a.CAPC = 0;
+  if (a.flat) {
+    // chunk partials reuse the block-score partials; at least 2048 chunks,
+    // more than any row holds (kMaxRowNnzBuild / kChunk)
+    a.CAPC = std::max<uint32_t>(2048u, (a.exhaustive ? 0u : nw * a.BMAX));
+    if (a.exhaustive || nw * a.BMAX < a.CAPC) {
+      a.off_part = take(a.CAPC * 4);  // the earlier part region is too small: a fresh one
+    }
+    a.off_fdoc = take(a.CAND * 4);
+    a.off_fc0 = take(a.CAND * 4);
+    a.off_fpre = take((a.CAND + 1) * 4);
+    a.off_cmap = take(a.CAPC);
+  }
   return o;
 }
 
 int launch_search(const SearchArgs &a, uint32_t group, uint32_t nw, size_t smem, uint32_t grid, cudaStream_t st) {
 #define SZ_CASE(G_, NW_) \
   if (group == G_ && nw == NW_) return launch_t<G_, NW_>(a, smem, grid, st);
+  SZ_CASE(1, 4) SZ_CASE(1, 8) SZ_CASE(1, 16)
   SZ_CASE(8, 4) SZ_CASE(8, 8) SZ_CASE(8, 16)
   SZ_CASE(16, 4) SZ_CASE(16, 8) SZ_CASE(16, 16)
   SZ_CASE(32, 4) SZ_CASE(32, 8) SZ_CASE(32, 16)
 #undef SZ_CASE
-  return fail(SEISMIC_EINVAL, "group must be 8/16/32 and cta_warps 4/8/16");
+  return fail(SEISMIC_EINVAL, "group must be 1/8/16/32 and cta_warps 4/8/16");
 }
 
 int search_occupancy(uint32_t group, uint32_t nw, size_t smem, int *blocks) {
 #define SZ_CASE(G_, NW_) \
   if (group == G_ && nw == NW_) return occupancy_t<G_, NW_>(smem, blocks);
+  SZ_CASE(1, 4) SZ_CASE(1, 8) SZ_CASE(1, 16)
   SZ_CASE(8, 4) SZ_CASE(8, 8) SZ_CASE(8, 16)
   SZ_CASE(16, 4) SZ_CASE(16, 8) SZ_CASE(16, 16)
   SZ_CASE(32, 4) SZ_CASE(32, 8) SZ_CASE(32, 16)
 #undef SZ_CASE
-  return fail(SEISMIC_EINVAL, "group must be 8/16/32 and cta_warps 4/8/16");
+  return fail(SEISMIC_EINVAL, "group must be 1/8/16/32 and cta_warps 4/8/16");
 }
 
 }  // namespace seismic

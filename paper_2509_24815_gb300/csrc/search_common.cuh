@@ -100,11 +100,16 @@ __device__ __forceinline__ void prefetch_row(const uint8_t *fwd, unsigned long l
 }
 
 // Document sources: id(i), and row(i, id) = first chunk | chunks << 32.
+// fetch(i, d, row) reads both with independent loads.
 struct MemberSrc {  // a contiguous range of block members (ids and rows side by side)
   const uint32_t *ids;
   const unsigned long long *rows;
   __device__ __forceinline__ uint32_t id(uint32_t i) const { return __ldg(ids + i); }
   __device__ __forceinline__ unsigned long long row(uint32_t i, uint32_t) const { return __ldg(rows + i); }
+  __device__ __forceinline__ void fetch(uint32_t i, uint32_t &d, unsigned long long &r) const {
+    d = __ldg(ids + i);
+    r = __ldg(rows + i);
+  }
 };
 
 struct GraphSrc {  // the kappa-NN neighbours of the ids in S
@@ -117,6 +122,10 @@ struct GraphSrc {  // the kappa-NN neighbours of the ids in S
     if (d == SEISMIC_NONE_ID) return 0ull;
     const uint32_t c0 = __ldg(cptr + d);
     return (unsigned long long)c0 | ((unsigned long long)(__ldg(cptr + d + 1) - c0) << 32);
+  }
+  __device__ __forceinline__ void fetch(uint32_t x, uint32_t &d, unsigned long long &r) const {
+    d = id(x);
+    r = row(x, d);
   }
 };
 
@@ -134,6 +143,11 @@ struct WaveSrc {
   }
   __device__ __forceinline__ uint32_t id(uint32_t i) const { return __ldg(ids + at(i)); }
   __device__ __forceinline__ unsigned long long row(uint32_t i, uint32_t) const { return __ldg(rows + at(i)); }
+  __device__ __forceinline__ void fetch(uint32_t i, uint32_t &d, unsigned long long &r) const {
+    const uint32_t m = at(i);
+    d = __ldg(ids + m);
+    r = __ldg(rows + m);
+  }
 };
 
 }  // namespace dev

@@ -53,10 +53,14 @@ struct SearchArgs {
   float sum_absmax;
   uint32_t prefetch;  // rows of the next block prefetched into L2 (at most this many; 0 = off)
   const uint32_t *perm;  // persistent launches pull queries in this order (NULL: 0, 1, 2, ...)
+  // CTA kernel, group 1: documents are scored chunk by chunk by all threads
+  // of the CTA (a wave's chunks laid end to end, then summed per document)
+  uint32_t flat;
   // shared-memory layout
-  uint32_t W, QN, BMAX, BPOW2, HS, CAND;
+  uint32_t W, QN, BMAX, BPOW2, HS, CAND, CAPC;
   uint32_t off_qbits, off_qrank, off_qval, off_qterm, off_cut, off_aq, off_part, off_keys, off_clo, off_chi,
-      off_hash, off_tk_s, off_tk_id, off_tmp_s, off_tmp_id, off_cand_s, off_cand_id, off_cand_ok, off_wave;
+      off_hash, off_tk_s, off_tk_id, off_tmp_s, off_tmp_id, off_cand_s, off_cand_id, off_cand_ok, off_wave,
+      off_fdoc, off_fc0, off_fpre, off_cmap, off_bptr;
 };
 
 constexpr uint32_t kMaxWave = 64;  // blocks per wave (CTA kernel)

@@ -26,52 +26,8 @@ NONE = oracle.NONE_ID
 TOL = 1e-5
 
 
-@pytest.fixture(scope="module")
-def sz():
-    import torch
-    assert torch.cuda.is_available(), "GPU tests need a GPU"
-    import __graft_entry__
-    __graft_entry__.build()
-    import paper_2509_24815_gb300 as m
-    return m
-
-
 def f32(x):
     return float(np.float32(x))
-
-
-def _mk(n_docs, n_q, d, K, seed=11):
-    return synth.docs(n_docs, seed=seed, d=d, K=K), synth.queries(n_q, seed=seed, d=d, K=K)
-
-
-@pytest.fixture(scope="module")
-def small(sz):
-    docs, queries = _mk(8000, 200, 4000, 24)
-    return dict(docs=docs, queries=queries, lam=150, beta=12, alpha=0.4)
-
-
-@pytest.fixture(scope="module")
-def small_built(sz, small):
-    out = {}
-    for quant in (True, False):
-        ix = sz.seismic_build(small["docs"], lambda_=small["lam"], beta=small["beta"], alpha=small["alpha"],
-                              quantize_u8=quant, seed=5, keep_full_lists=True, keep_block_summaries=True)
-        ox = oracle.Index(small["docs"], small["lam"], small["beta"], small["alpha"], quant, seed=5)
-        out[quant] = (ix, ox)
-    return out
-
-
-@pytest.fixture(scope="module")
-def c1(sz):
-    """The tiny Seismic configuration: 100k docs, lambda=2000, beta=100,
-    alpha=0.4, fp32 summaries, 1k queries (seed 0)."""
-    docs = synth.docs(100_000, seed=0)
-    queries = synth.queries(1000, seed=0)
-    ix = sz.seismic_build(docs, lambda_=2000, beta=100, alpha=0.4, quantize_u8=False, seed=0,
-                          keep_full_lists=True, keep_block_summaries=True)
-    ox = oracle.Index(docs, 2000, 100, 0.4, False, seed=0)
-    ei, es = oracle.exact_topk(docs, queries, 10)
-    return dict(docs=docs, queries=queries, ix=ix, ox=ox, ei=ei, es=es)
 
 
 def compare_index(sz, ix, ox, dim, quant):
@@ -411,8 +367,10 @@ def test_errors_leave_the_index_usable(sz, small, small_built):
         sz.seismic_search(ix, nan, k=5)
     with pytest.raises(sz.SeismicError):
         sz.seismic_search(ix, synth.CSR(q.indptr, q.terms, q.vals, q.dim + 1), k=5)
+    fresh = sz.seismic_build(small["docs"].slice(0, 500), lambda_=50, beta=5, alpha=0.4)
     with pytest.raises(sz.SeismicError):
-        sz.seismic_search(ix, q, k=5, learned=True)  # no MLP installed on this index
+        sz.seismic_search(fresh, q, k=5, learned=True)  # no MLP installed on this index
+    fresh.close()
     with pytest.raises(sz.SeismicError):
         sz.seismic_build(small["docs"], alpha=0.0)
     gi, _ = sz.seismic_search(ix, q, k=5, cut=3)
