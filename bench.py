@@ -52,6 +52,9 @@ WORKLOADS = {
 }
 RECALL_TARGET = 0.9
 K = 10
+# DRAM bytes (read + write) of one search launch, from one ncu capture of this kernel version on the
+# named workload and launch configuration (profiles/k_search_flat_c2_dram.md); any other case: null
+MEASURED_TRAFFIC = {("c2", 1, 8, 16, False): 179.63e9}
 
 
 def log(*a):
@@ -183,10 +186,21 @@ def learned_eval(args, w, sz, ix, dq, gt_sc, stream, time_runs, launch):
             fine.append(dict(cut=cut, heap_factor=hf, **measure(cut=cut, heap_factor=hf)))
     at = [f for f in fine if f["recall"] >= lr["recall"] - 1e-9]
     ref = max(at, key=lambda f: f["qps"]) if at else max(fine, key=lambda f: f["recall"])
+    # the fixed form's recall/QPS frontier, interpolated linearly at the learned recall
+    front = sorted(fine, key=lambda f: f["recall"])
+    front = [f for i, f in enumerate(front) if all(g["qps"] < f["qps"] for g in front[i + 1:])]
+    interp = None
+    for f0, f1 in zip(front, front[1:]):
+        if f0["recall"] <= lr["recall"] <= f1["recall"]:
+            t = (lr["recall"] - f0["recall"]) / max(f1["recall"] - f0["recall"], 1e-12)
+            interp = f0["qps"] + t * (f1["qps"] - f0["qps"])
     log(f"learned: recall {lr['recall']:.4f} at {lr['qps']:,.0f} q/s; best fixed at >= that recall: "
-        f"cut={ref['cut']} hf={ref['heap_factor']} recall {ref['recall']:.4f} at {ref['qps']:,.0f} q/s")
+        f"cut={ref['cut']} hf={ref['heap_factor']} recall {ref['recall']:.4f} at {ref['qps']:,.0f} q/s; "
+        f"fixed frontier at that recall: {interp if interp is None else round(interp)} q/s")
     return {"value": lr["qps"], "unit": "queries/s", "recall@10": lr["recall"], "ms_per_step": lr["ms"],
             "fixed_at_equal_recall": ref, "qps_gain_vs_fixed": lr["qps"] / ref["qps"],
+            "fixed_frontier_qps_at_learned_recall": interp,
+            "qps_gain_vs_fixed_frontier": (lr["qps"] / interp) if interp else None,
             "train_queries": tq.n_rows, "label_target_recall": args.learn_target, "fit_seconds": t_fit,
             "final_loss": res["trace"][-1][1], "label_mean_recall": res["label_recall"],
             "calibration_shift": res["calib_shift"], "validation_recall": res["val_recall"],
@@ -430,7 +444,9 @@ def main():
         "grid": grid,
         "autotune": tuned,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "peak_source": peak_kind,
+                     "traffic": MEASURED_TRAFFIC.get((args.workload, launch["group"], launch["cta_warps"] or 8,
+                                                      launch["wave"], launch["no_prefetch"])),
+                     "peak_source": peak_kind,
                      "alg_bytes_per_launch": alg_bytes, "kernel": "k_search"},
         "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": args.steps * launches_per_step,

@@ -147,23 +147,37 @@ def predict(weights: np.ndarray, features: np.ndarray):
 
 
 def calibrate(index, weights: np.ndarray, queries: DeviceCSR, gt_scores, k: int, target: float,
-              quantized: bool, base_params=None, shifts=(0.0, 0.15, 0.3, 0.45, 0.6, 0.8, 1.0, 1.3, 1.6, 2.0)):
+              quantized: bool, base_params=None, margin: float = 0.005, max_shift: float = 6.0, iters: int = 10):
     """Shifts the cut output's bias (logit units) so that the learned form's
-    mean recall on held-out training queries reaches `target`, taking the
-    smallest shift that does (the least work).  Returns (weights, shift, recall)."""
+    mean recall on held-out training queries reaches `target + margin`: the
+    smallest such shift in [0, max_shift] (the least work), found by bisection
+    (recall grows with the shift).  Returns (weights, shift, recall)."""
     base = dict(base_params or {})
     b3 = MLP_PARAMS - 2
-    best = None
-    for s in shifts:
+    goal = target + margin
+
+    def run(shift):
         w = weights.copy()
-        w[b3] += np.float32(s)
+        w[b3] += np.float32(shift)
         seismic_set_mlp(index, w)
         ids, sc = seismic_search(index, queries, search_params(k=k, cut=10, heap_factor=0.8, learned=True,
                                                                max_query_nnz=queries.max_row_nnz, **base))
-        rec = float(recall_at_k(ids.cpu().numpy().view(np.uint32), sc.cpu().numpy(), gt_scores, k).mean())
-        best = (w, s, rec)
-        if rec >= target:
-            break
+        return w, float(recall_at_k(ids.cpu().numpy().view(np.uint32), sc.cpu().numpy(), gt_scores, k).mean())
+
+    w0, r0 = run(0.0)
+    if r0 >= goal:
+        return w0, 0.0, r0
+    whi, rhi = run(max_shift)
+    if rhi < goal:
+        return whi, max_shift, rhi
+    lo, hi, best = 0.0, max_shift, (whi, max_shift, rhi)
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        w, r = run(mid)
+        if r >= goal:
+            hi, best = mid, (w, mid, r)
+        else:
+            lo = mid
     return best
 
 
