@@ -48,7 +48,8 @@ WORKLOADS = {
     "c3": dict(desc="Seismic 8.8M docs, vocab 30522, lambda=6000, beta=400, alpha=0.4, u8 summaries, kappa=10, "
                     "10k queries (uniform nnz 10-150), k=10", n_docs=8_800_000, n_q=10_000, uneven=True, lam=6000,
                beta=400, alpha=0.4, quant=True, cuts=(5, 10, 20), hfs=(0.6, 0.7, 0.8, 0.9), kappa=10,
-               cpu_sample=100),
+               cpu_sample=100, n_train=20_000, serve_rates=(5_000, 50_000, 100_000, 200_000),
+               fine_cuts=(5, 8, 10, 12, 16, 20, 25, 30)),
 }
 RECALL_TARGET = 0.9
 K = 10
@@ -149,9 +150,57 @@ def cpu_baseline(w, docs, queries, cut, hf, steps=1):
         ox.search(sample, K, cut=cut, heap_factor=float(np.float32(hf)), threads=threads)
         times.append(time.perf_counter() - t0)
     qps = n / float(np.median(times))
+    # the paper's protocol: one thread, mean time per query (a smaller sample)
+    n1 = max(1, min(n, 20))
+    t0 = time.perf_counter()
+    ox.search(sample.slice(0, n1), K, cut=cut, heap_factor=float(np.float32(hf)), threads=1)
+    us1 = (time.perf_counter() - t0) / n1 * 1e6
     return {"value": qps, "unit": "queries/s", "cores": threads, "kind": "oracle",
             "sample": f"first {n} of the {queries.n_rows} queries, cut={cut}, heap_factor={hf}, one query per "
-                      f"thread; lists built untimed", "times_s": times}
+                      f"thread; lists built untimed", "times_s": times,
+            "single_thread_us_per_query": us1, "single_thread_sample": n1}
+
+
+def sample_parity(w, ix, docs, queries, gt_ids, gt_sc, ids, sc, sz, n_q=200, n_nodes=1000):
+    """Full-size parity on sampled outputs, against the oracle: the device's
+    exact top-10 (the recall judge) and the timed configuration's returned
+    scores on a sample of queries, and the kappa-NN graph on a sample of nodes."""
+    import oracle
+    t = time.time()
+    rng = np.random.default_rng(7)
+    qs = np.sort(rng.choice(queries.n_rows, min(n_q, queries.n_rows), replace=False))
+    sub = queries.take(qs)
+    ei, es = oracle.exact_topk(docs, sub, K)
+    gi = gt_ids[qs].view(np.uint32)
+    gs = gt_sc[qs].astype(np.float64)
+    # exact top-10: ids equal up to near-ties, scores within 1e-5 of fp64
+    qi = np.repeat(np.arange(len(qs), dtype=np.uint64), K)
+    ex = oracle.pair_dots(docs, sub, qi, gi.reshape(-1)).reshape(gi.shape)
+    rel_exact = float(np.max(np.abs(gs - ex) / np.maximum(np.abs(ex), 1e-30)))
+    same = gi == ei
+    tie_ok = bool(np.all(same | (np.abs(ex - es) <= 2e-5 * np.abs(es))))
+    # the timed configuration: each returned score is the exact inner product of its id
+    ri = ids[qs].view(np.uint32)
+    valid = ri != oracle.NONE_ID
+    rs = oracle.pair_dots(docs, sub, np.repeat(np.arange(len(qs), dtype=np.uint64), K)[valid.reshape(-1)],
+                          ri[valid])
+    rel_search = float(np.max(np.abs(sc[qs][valid] - rs) / np.maximum(np.abs(rs), 1e-30), initial=0.0))
+    out = {"queries": int(len(qs)), "exact_ids_equal": float(same.mean()), "exact_ties_only": tie_ok,
+           "exact_max_rel_err": rel_exact, "search_scores_max_rel_err": rel_search}
+    if w["kappa"]:
+        nodes = np.sort(rng.choice(docs.n_rows, min(n_nodes, docs.n_rows), replace=False))
+        ni, _ = oracle.exact_topk(docs, docs.take(nodes), w["kappa"] + 1)
+        g = sz.seismic_get_knn(ix)[nodes]
+        rec = []
+        for r, row in enumerate(ni):
+            truth = [x for x in row if x != nodes[r]][: w["kappa"]]
+            rec.append(len(set(truth) & set(g[r].tolist())) / w["kappa"])
+        out["knn_nodes"] = int(len(nodes))
+        out["knn_graph_recall"] = float(np.mean(rec))
+        out["knn_self_loops"] = int(np.sum(g == nodes[:, None]))
+    out["seconds"] = time.time() - t
+    log(f"sample parity: {out}")
+    return out
 
 
 def learned_eval(args, w, sz, ix, dq, gt_sc, stream, time_runs, launch):
@@ -181,7 +230,7 @@ def learned_eval(args, w, sz, ix, dq, gt_sc, stream, time_runs, launch):
 
     lr = measure(cut=10, heap_factor=0.8, learned=True)
     fine = []
-    for cut in (3, 4, 5, 6, 8, 10):
+    for cut in w.get("fine_cuts", (3, 4, 5, 6, 8, 10)):
         for hf in (0.6, 0.7, 0.8, 0.9, 1.0):
             fine.append(dict(cut=cut, heap_factor=hf, **measure(cut=cut, heap_factor=hf)))
     at = [f for f in fine if f["recall"] >= lr["recall"] - 1e-9]
@@ -307,7 +356,8 @@ def main():
     log(f"exact top-{K} (device brute force) in {time.time() - t:.1f}s")
     if w["kappa"]:
         t = time.time()
-        sz.seismic_build_knn(ix, w["kappa"], sz.search_params(k=w["kappa"] + 1, cut=10, heap_factor=0.9))
+        sz.seismic_build_knn(ix, w["kappa"], sz.search_params(k=w["kappa"] + 1, cut=10, heap_factor=0.9, shape=1,
+                                                              group=1, wave=16, persistent=True))
         log(f"kappa-NN graph built in {time.time() - t:.1f}s")
 
     stream = torch.cuda.Stream()
@@ -454,13 +504,18 @@ def main():
         "index": {k: info[k] for k in ("n_docs", "nnz", "n_postings", "n_blocks", "n_summary_entries",
                                        "device_bytes")},
     }
+    run(p)
+    stream.synchronize()
+    line["parity_sample"] = sample_parity(w, ix, docs, queries, gt_ids.cpu().numpy(), gt_sc, ids.cpu().numpy(),
+                                          sc.cpu().numpy(), sz)
     if not args.no_learned and w.get("n_train"):
         line["learned"] = learned_eval(args, w, sz, ix, dq, gt_sc, stream, time_runs, launch)
     if not args.no_serve and w.get("serve_rates"):
         line["serving"] = serving_eval(args, w, sz, ix, best, bool(line.get("learned")), launch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(w, docs, queries, best["cut"], best["heap_factor"])
-        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample",
+                                                   "single_thread_us_per_query", "single_thread_sample")}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

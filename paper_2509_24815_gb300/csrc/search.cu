@@ -242,9 +242,12 @@ __device__ void eval_wave(const SearchArgs &a, Smem &s, Shared &sh, uint32_t n, 
 }
 
 // v[0..n) -> exclusive prefix sums, v[n] = the total (n <= 32 * NT).  Starts
-// and ends with a barrier-separated phase; every thread must call it.
+// and ends with a barrier-separated phase; every thread must call it.  When
+// map is given and the total is at most cap, also writes map[v[i] .. v[i+1])
+// = i (the owner of each unit, i < 256).
 template <int NT>
-__device__ uint32_t block_exclusive_scan(uint32_t *v, uint32_t n, uint32_t *wtmp) {
+__device__ uint32_t block_exclusive_scan(uint32_t *v, uint32_t n, uint32_t *wtmp, uint8_t *map = nullptr,
+                                         uint32_t cap = 0) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int nw = NT / 32;
   const uint32_t per = (n + NT - 1) / NT, lo = min(n, tid * per), hi = min(n, lo + per);
@@ -269,12 +272,15 @@ __device__ uint32_t block_exclusive_scan(uint32_t *v, uint32_t n, uint32_t *wtmp
   }
   __syncthreads();
   uint32_t run = (warp ? wtmp[warp - 1] : 0) + x - sum;
+  const uint32_t total = wtmp[nw - 1];
+  const bool fill = map != nullptr && total <= cap;
   for (uint32_t i = lo; i < hi; i++) {
     const uint32_t c = v[i];
     v[i] = run;
+    if (fill)
+      for (uint32_t u = 0; u < c; u++) map[run + u] = (uint8_t)i;
     run += c;
   }
-  const uint32_t total = wtmp[nw - 1];
   if (tid == 0) v[n] = total;
   __syncthreads();
   return total;
@@ -323,7 +329,8 @@ __device__ __forceinline__ void eval_wave_flat(const SearchArgs &a, Smem &s, Sha
     s.fpre()[i] = nch;
   }
   __syncthreads();
-  block_exclusive_scan<NT>(s.fpre(), n, sh.wtmp);
+  // the chunk map of a wave that fits one pass is written by the scan itself
+  const uint32_t all = block_exclusive_scan<NT>(s.fpre(), n, sh.wtmp, s.cmap(), a.CAPC);
   const uint32_t *qb = s.qbits();
   const uint16_t *qr = s.qrank();
   const float *qv = s.qval();
@@ -337,11 +344,13 @@ __device__ __forceinline__ void eval_wave_flat(const SearchArgs &a, Smem &s, Sha
       if (s.fpre()[mid] - base <= a.CAPC) lo = mid; else hi = mid - 1;
     }
     const uint32_t i1 = lo, total = s.fpre()[i1] - base;
-    for (uint32_t i = i0 + tid; i < i1; i += NT) {
-      const uint32_t e = s.fpre()[i + 1] - base;
-      for (uint32_t c = s.fpre()[i] - base; c < e; c++) s.cmap()[c] = (uint8_t)i;  // i < CAND <= 256
+    if (all > a.CAPC) {  // several passes: map this one
+      for (uint32_t i = i0 + tid; i < i1; i += NT) {
+        const uint32_t e = s.fpre()[i + 1] - base;
+        for (uint32_t c = s.fpre()[i] - base; c < e; c++) s.cmap()[c] = (uint8_t)i;  // i < CAND <= 256
+      }
+      __syncthreads();
     }
-    __syncthreads();
 #pragma unroll 1
     for (uint32_t j = tid; j < total; j += NT * U) {
       uint4 t[U], va[U], vb[U];

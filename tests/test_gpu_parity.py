@@ -488,3 +488,27 @@ def test_learned_search_uses_mlp_params(sz, small, small_built):
             assert len(set(a[0].tolist()) & set(gi[i].tolist())) >= 8
         checked += 1
     assert checked > q.n_rows // 2
+
+
+# ------------------------------------------------------------------ proportional lists (Set alpha-MSS) and fractional beta
+@pytest.mark.parametrize("lam_frac,beta_frac,quant", [(0.3, 0.05, True), (0.6, 0.0, False), (0.0, 0.1, True)])
+def test_proportional_lists_and_fractional_beta(sz, small, lam_frac, beta_frac, quant):
+    """lambda_t = ceil(lambda_frac * |L_t|) (Definition Set alpha-MSS, Section 3.3) and
+    ceil(beta_frac * |list|) clusters per list: the same index as the oracle's,
+    and search parity on it."""
+    docs, queries = small["docs"], small["queries"]
+    ix = sz.seismic_build(docs, lambda_=small["lam"], beta=small["beta"], alpha=0.4, quantize_u8=quant, seed=3,
+                          lambda_frac=lam_frac, beta_frac=beta_frac, keep_full_lists=True,
+                          keep_block_summaries=True)
+    ox = oracle.Index(docs, small["lam"], small["beta"], 0.4, quant, seed=3, lambda_frac=lam_frac,
+                      beta_frac=beta_frac)
+    compare_index(sz, ix, ox, docs.dim, quant)
+    gi, gs = sz.seismic_search(ix, queries, k=10, cut=5, exhaustive=True, shape=1, group=1)
+    ref = ox.search(queries, 10, cut=5, exhaustive=True)
+    check_exact_ids(docs, queries, gi, gs, ref["ids"], ref["scores"])
+    ei, es = oracle.exact_topk(docs, queries, 10)
+    gi, gs = sz.seismic_search(ix, queries, k=10, cut=5, heap_factor=0.9)
+    ref = ox.search(queries, 10, cut=5, heap_factor=f32(0.9))
+    assert abs(oracle.recall_at_k(docs, queries, gi, es, 10).mean()
+               - oracle.recall_at_k(docs, queries, ref["ids"], es, 10).mean()) <= 0.005
+    ix.close()
