@@ -69,3 +69,39 @@ def test_fullsize_bench_configuration(sz, full):
     _, _, st = sz.seismic_search(full["ix"], sub, p1, stats=True)
     same = (st[:, sz.STATS.index("blocks_evaluated")] == ref["stats"][:, 2]).mean()
     assert same >= 0.95, same
+
+
+def test_fullsize_learned_parameters_gain(sz, full):
+    """What the trained network gains over the method without it: per-query
+    (cut, heap_factor) from the MLP, trained on separate training queries with
+    the library's own kernels, against the fixed-parameter form's work/recall
+    frontier at the same recall, on held-out queries.  Work is the search's
+    algorithmic bytes (deterministic, from its own counters)."""
+    from paper_2509_24815_gb300 import learn, metrics
+    ix = full["ix"]
+    train = synth.queries(20_000, seed=0, uneven=True, stream=synth.TRAIN_STREAM)
+    held = synth.queries(2_000, seed=0, uneven=True, stream=synth.HELDOUT_STREAM)
+    base = dict(shape=1, group=1, cta_warps=8, wave=16, persistent=True)
+    learn.fit(ix, sz.DeviceCSR.from_host(train), train, k=10, target=0.9, quantized=True, steps=3000,
+              base_params=base)
+    _, gt = sz.seismic_search_exact(ix, held, 10)
+
+    def run(**kw):
+        ids, sc, st = sz.seismic_search(ix, held, sz.search_params(k=10, **base, **kw), stats=True)
+        rec = float(metrics.recall_at_k(ids, sc, gt, 10).mean())
+        return rec, float(metrics.algorithmic_bytes(st, 10, True).mean())
+
+    r_l, b_l = run(cut=10, heap_factor=0.8, learned=True)
+    pts = sorted(run(cut=c, heap_factor=h) for c in (3, 4, 5, 6, 8, 10, 12) for h in (0.6, 0.8, 1.0))
+    # lower envelope of bytes over recall, interpolated linearly at the learned recall
+    front = [p for i, p in enumerate(pts) if all(q[1] > p[1] for q in pts[i + 1:])]
+    b_f = None
+    for (r0, b0), (r1, b1) in zip(front, front[1:]):
+        if r0 <= r_l <= r1:
+            b_f = b0 + (r_l - r0) / max(r1 - r0, 1e-12) * (b1 - b0)
+    assert b_f is not None, (r_l, front)
+    gain = b_f / b_l
+    print(f"learned: recall {r_l:.4f} at {b_l / 1e6:.2f} MB/query; fixed frontier {b_f / 1e6:.2f} MB/query; "
+          f"gain {gain:.3f}")
+    assert r_l >= 0.89, r_l
+    assert gain >= 1.0, gain
