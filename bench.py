@@ -53,6 +53,7 @@ WORKLOADS = {
 }
 RECALL_TARGET = 0.9
 K = 10
+METRIC = "QPS at recall@10>=0.9 (batched Seismic search, fixed parameters)"
 # DRAM bytes (read + write) of one search launch, from one ncu capture of this kernel version on the
 # named workload and launch configuration (profiles/k_search_flat_c2_dram.md); any other case: null
 MEASURED_TRAFFIC = {("c2", 1, 8, 16, False): 179.63e9}
@@ -289,7 +290,7 @@ def run_reference(args, w):
     docs, queries = make_data(w)
     cut, hf = (5, 0.9) if len(w["cuts"]) > 1 else (w["cuts"][0], w["hfs"][0])
     cb = cpu_baseline(w, docs, queries, cut, hf, steps=max(1, args.steps))
-    line = {"impl": "reference", "metric": "QPS at recall@10>=0.9 (batched Seismic search)", "value": cb["value"],
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"],
             "unit": "queries/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * float(np.median(cb["times_s"])), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -483,7 +484,7 @@ def main():
     peak, peak_kind = peaks()
     achieved = alg_bytes / (float(np.mean(per)) * 1e-3) / 1e9  # this rank's kernel, per launch
     line = {
-        "metric": "QPS at recall@10>=0.9 (batched Seismic search, fixed parameters)",
+        "metric": METRIC,
         "value": qps, "unit": "queries/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",

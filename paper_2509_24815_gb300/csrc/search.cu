@@ -120,13 +120,11 @@ struct Smem {
   __device__ __forceinline__ uint32_t *tmp_id() const { return reinterpret_cast<uint32_t *>(g_sm + a.off_tmp_id); }
   __device__ __forceinline__ uint32_t *cand_id() const { return reinterpret_cast<uint32_t *>(g_sm + a.off_cand_id); }
   __device__ __forceinline__ uint8_t *cand_ok() const { return reinterpret_cast<uint8_t *>(g_sm + a.off_cand_ok); }
-  __device__ __forceinline__ uint32_t *woff() const { return reinterpret_cast<uint32_t *>(g_sm + a.off_wave); }
   __device__ __forceinline__ uint32_t *bptr() const { return reinterpret_cast<uint32_t *>(g_sm + a.off_bptr); }
   __device__ __forceinline__ uint32_t *fdoc() const { return reinterpret_cast<uint32_t *>(g_sm + a.off_fdoc); }
   __device__ __forceinline__ uint32_t *fc0() const { return reinterpret_cast<uint32_t *>(g_sm + a.off_fc0); }
   __device__ __forceinline__ uint32_t *fpre() const { return reinterpret_cast<uint32_t *>(g_sm + a.off_fpre); }
   __device__ __forceinline__ uint8_t *cmap() const { return reinterpret_cast<uint8_t *>(g_sm + a.off_cmap); }
-  __device__ __forceinline__ uint32_t *wstart() const { return woff() + (kMaxWave + 1); }
 };
 
 struct Shared {
@@ -135,6 +133,34 @@ struct Shared {
   uint32_t cut;
   uint32_t wtmp[32];
   unsigned long long st[SEISMIC_STATS_N];
+};
+
+// The members of the wave's blocks keys[0 .. nw) (sorted positions) of the
+// current list, as one run: member i is found by walking the blocks' sizes in
+// shared memory, so forming a wave needs no barrier.
+struct WaveBlocks {
+  const unsigned long long *keys;
+  const uint32_t *bptr;
+  uint32_t nw;
+  const uint32_t *ids;
+  const unsigned long long *rows;
+  __device__ __forceinline__ uint32_t at(uint32_t i) const {
+    uint32_t b = (uint32_t)(keys[0] & 0xFFFFFFFFu), lo = bptr[b], nd = bptr[b + 1] - lo;
+    for (uint32_t w = 1; w < nw && i >= nd; w++) {
+      i -= nd;
+      b = (uint32_t)(keys[w] & 0xFFFFFFFFu);
+      lo = bptr[b];
+      nd = bptr[b + 1] - lo;
+    }
+    return lo + i;
+  }
+  __device__ __forceinline__ uint32_t id(uint32_t i) const { return __ldg(ids + at(i)); }
+  __device__ __forceinline__ unsigned long long row(uint32_t i, uint32_t) const { return __ldg(rows + at(i)); }
+  __device__ __forceinline__ void fetch(uint32_t i, uint32_t &d, unsigned long long &r) const {
+    const uint32_t m = at(i);
+    d = __ldg(ids + m);
+    r = __ldg(rows + m);
+  }
 };
 
 template <int NT>
@@ -656,18 +682,7 @@ __global__ void __launch_bounds__(NW * 32, 1280 / (NW * 32))
             eval<G, NT>(a, s, sh, min(a.CAND, d1 - c0), src, 0);
           }
         } else {
-          if (tid == 0) {
-            uint32_t acc = 0;
-            for (uint32_t w = 0; w < be - bi; w++) {
-              const uint32_t b = (uint32_t)(s.keys()[bi + w] & 0xFFFFFFFFu);
-              s.woff()[w] = acc;
-              s.wstart()[w] = s.bptr()[b];
-              acc += s.bptr()[b + 1] - s.bptr()[b];
-            }
-            s.woff()[be - bi] = acc;
-          }
-          __syncthreads();
-          const WaveSrc src{s.woff(), s.wstart(), be - bi, a.bdoc, a.bdoc_row};
+          const WaveBlocks src{s.keys() + bi, s.bptr(), be - bi, a.bdoc, a.bdoc_row};
           eval<G, NT>(a, s, sh, ndocs, src, 0);
         }
         bi = be;
@@ -757,7 +772,6 @@ size_t search_layout(SearchArgs &a, uint32_t nw) {
   a.off_cand_s = take(a.CAND * 4);
   a.off_cand_id = take(a.CAND * 4);
   a.off_cand_ok = take(a.CAND);
-  a.off_wave = take(2 * (kMaxWave + 1) * 4);
   a.off_bptr = take(a.exhaustive ? 4 : (a.BMAX + 1) * 4);
   a.CAPC = 0;
   if (a.flat) {

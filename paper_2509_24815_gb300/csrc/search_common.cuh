@@ -129,26 +129,5 @@ struct GraphSrc {  // the kappa-NN neighbours of the ids in S
   }
 };
 
-// the members of several blocks: block w covers wave positions [off[w], off[w+1])
-// and member indices from start[w]
-struct WaveSrc {
-  const uint32_t *off, *start;
-  uint32_t nw;
-  const uint32_t *ids;
-  const unsigned long long *rows;
-  __device__ __forceinline__ uint32_t at(uint32_t i) const {
-    uint32_t w = 0;
-    while (w + 1 < nw && off[w + 1] <= i) w++;
-    return start[w] + (i - off[w]);
-  }
-  __device__ __forceinline__ uint32_t id(uint32_t i) const { return __ldg(ids + at(i)); }
-  __device__ __forceinline__ unsigned long long row(uint32_t i, uint32_t) const { return __ldg(rows + at(i)); }
-  __device__ __forceinline__ void fetch(uint32_t i, uint32_t &d, unsigned long long &r) const {
-    const uint32_t m = at(i);
-    d = __ldg(ids + m);
-    r = __ldg(rows + m);
-  }
-};
-
 }  // namespace dev
 }  // namespace seismic
