@@ -97,7 +97,8 @@ typedef struct {
                             takes row chunks of the whole wave (chunk-flattened; seen documents
                             are dropped before their rows are read), 8/16/32 = lane groups of
                             that width score one row each.  Warp shape: 4/8/16/32 lanes per
-                            row.  0 = 8.  Scores differ only in fp32 summation order */
+                            row.  0 = 1 on the CTA shape, 8 on the warp shape.  Scores differ
+                            only in fp32 summation order */
   uint32_t cta_warps;    /* warps per CTA: 4, 8 or 16; 0 = 8 */
   uint32_t persistent;   /* 1: one persistent launch that pulls queries from a device queue */
   uint32_t max_query_nnz; /* device queries: an upper bound on any query's nonzeros, which sizes
@@ -105,10 +106,10 @@ typedef struct {
                             inside stream capture).  Ignored for host queries. */
   uint32_t hash_slots;   /* per-query seen-set slots (power of two); 0 = 2048.  A full set only
                             costs repeated work, never a different result */
-  uint32_t shape;        /* 0 (auto): warp per query when k <= 128 and wave <= 1, else CTA per
-                            query; 1: one CTA per query (any k, any wave); 2: one warp per
-                            query (persistent, cta_warps independent warps per CTA: 1/2/4,
-                            0 = 4).  Both keep the algorithm's sequential order at wave 1 */
+  uint32_t shape;        /* 0 or 1: one CTA per query (any k, any wave; the measured fastest);
+                            2: one warp per query (k <= 128, wave 1, persistent, cta_warps
+                            independent warps per CTA: 1/2/4, 0 = 4).  Both keep the
+                            algorithm's sequential order at wave 1 */
   int32_t no_prefetch;   /* 1 turns off the L2 bulk prefetch of upcoming member lists and rows
                             (a speed knob; results are the same) */
   uint32_t order;        /* persistent launches: 0 (default) runs queries grouped by their

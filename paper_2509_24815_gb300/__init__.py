@@ -202,7 +202,7 @@ def seismic_build(docs, lambda_=2000, beta=100, alpha=0.4, quantize_u8=False, se
 
 
 def search_params(k=10, cut=10, heap_factor=0.8, hf_mode=0, exhaustive=False, alpha_q=0.0, use_knn=False,
-                  learned=False, wave=1, group=8, cta_warps=0, persistent=False, max_query_nnz=0,
+                  learned=False, wave=1, group=0, cta_warps=0, persistent=False, max_query_nnz=0,
                   hash_slots=0, shape=0, no_prefetch=False, order=0) -> SearchParams:
     return SearchParams(int(k), int(cut), float(heap_factor), int(hf_mode), int(bool(exhaustive)), float(alpha_q),
                         int(bool(use_knn)), int(bool(learned)), int(wave), int(group), int(cta_warps),

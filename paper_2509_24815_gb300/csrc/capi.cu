@@ -161,9 +161,9 @@ int check_params(const seismic_index *ix, const seismic_search_params *p) {
   if (p->hf_mode != 0 && p->hf_mode != 1) return fail(SEISMIC_EINVAL, "hf_mode must be 0 or 1");
   if (p->use_knn && ix->kappa == 0) return fail(SEISMIC_EINVAL, "use_knn: the index has no kappa-NN graph");
   if (p->learned && !ix->has_mlp) return fail(SEISMIC_EINVAL, "learned: the index has no MLP");
-  uint32_t g = p->group ? p->group : 8, w = p->cta_warps ? p->cta_warps : 8;
   if (p->shape > 2) return fail(SEISMIC_EINVAL, "shape must be 0 (auto), 1 (CTA per query) or 2 (warp per query)");
-  const bool ws = p->shape == 2 || (p->shape == 0 && p->k <= 128 && p->wave <= 1);
+  const bool ws = p->shape == 2;
+  uint32_t g = p->group ? p->group : (ws ? 8 : 1), w = p->cta_warps ? p->cta_warps : 8;
   if (!(g == 8 || g == 16 || g == 32 || (ws && g == 4) || (!ws && g == 1)))
     return fail(SEISMIC_EINVAL, "group must be 8/16/32 (4 also for the warp shape, 1 for the CTA shape)");
   const uint32_t ww = p->cta_warps ? p->cta_warps : 4;
@@ -262,10 +262,11 @@ int search_ws(seismic_index *ix, Workspace *w, const seismic_csr *queries, const
     a.q_hf = qh;
     a.QN = std::max<uint32_t>(a.QN, 32);
   }
-  const uint32_t nw = p->cta_warps ? p->cta_warps : 8, group = p->group ? p->group : 8;
+  // defaults: one CTA per query with chunk-flattened scoring (the measured fastest)
+  const uint32_t nw = p->cta_warps ? p->cta_warps : 8, group = p->group ? p->group : (p->shape == 2 ? 8 : 1);
   a.sum_absmax = ix->sum_absmax;
   a.prefetch = p->no_prefetch ? 0u : 256u;
-  const bool warp_shape0 = p->shape == 2 || (p->shape == 0 && k <= 128 && a.wave <= 1);
+  const bool warp_shape0 = p->shape == 2;
   if (p->order == 0 && nq > 1 && (a.persistent || warp_shape0)) {
     if ((rc = w->perm.ensure((size_t)nq * 12))) return rc;
     unsigned long long *keys = w->perm.as<unsigned long long>();
@@ -281,8 +282,8 @@ int search_ws(seismic_index *ix, Workspace *w, const seismic_csr *queries, const
     SZ_CUDA(cudaGetLastError());
     a.perm = perm;
   }
-  // shape: one warp per query (default when k <= 128 and wave = 1) or one CTA per query
-  const bool warp_shape = p->shape == 2 || (p->shape == 0 && k <= 128 && a.wave <= 1);
+  // shape: one CTA per query (default) or one warp per query
+  const bool warp_shape = p->shape == 2;
   if (warp_shape) {
     if (k > 128) return fail(SEISMIC_EINVAL, "the warp-per-query shape needs k <= 128");
     const uint32_t wpb = p->cta_warps ? p->cta_warps : 4;

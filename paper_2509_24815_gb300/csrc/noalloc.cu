@@ -56,9 +56,9 @@ extern "C" int seismic_search_noalloc(seismic_index *ix, const seismic_csr *quer
   if (!p->exhaustive && !(p->heap_factor > 0.0f)) return fail(SEISMIC_EINVAL, "heap_factor must be > 0");
   if (p->hf_mode != 0 && p->hf_mode != 1) return fail(SEISMIC_EINVAL, "hf_mode must be 0 or 1");
   if (p->use_knn && ix->kappa == 0) return fail(SEISMIC_EINVAL, "use_knn: the index has no kappa-NN graph");
-  const uint32_t group = p->group ? p->group : 8, nw = p->cta_warps ? p->cta_warps : 8;
-  if (!(group == 8 || group == 16 || group == 32) || !(nw == 4 || nw == 8 || nw == 16))
-    return fail(SEISMIC_EINVAL, "noalloc search: group must be 8/16/32 and cta_warps 4/8/16");
+  const uint32_t group = p->group ? p->group : 1, nw = p->cta_warps ? p->cta_warps : 8;
+  if (!(group == 1 || group == 8 || group == 16 || group == 32) || !(nw == 4 || nw == 8 || nw == 16))
+    return fail(SEISMIC_EINVAL, "noalloc search: group must be 1/8/16/32 and cta_warps 4/8/16");
   if (queries->n_rows == 0) return SEISMIC_OK;
   if (queries->n_rows > 0x7FFFFFFFull) return fail(SEISMIC_EINVAL, "too many queries in one call");
   const uint64_t words = ((ix->n_docs + 31) / 32 + 3) & ~3ull;

@@ -244,7 +244,7 @@ int seismic_server_create(seismic_index *ix, const seismic_search_params *search
       a.CAND = 256;
       a.k = std::max<uint32_t>(search->k, 100);
       a.alpha_q = search->alpha_q;
-      const uint32_t nw = search->cta_warps ? search->cta_warps : 8, g = search->group ? search->group : 8;
+      const uint32_t nw = search->cta_warps ? search->cta_warps : 8, g = search->group ? search->group : 1;
       a.dim = ix->dim;
       a.flat = g == 1 ? 1u : 0u;
       size_t smem = search_layout(a, nw);
