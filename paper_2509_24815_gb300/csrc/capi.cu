@@ -273,11 +273,8 @@ int search_ws(seismic_index *ix, Workspace *w, const seismic_csr *queries, const
     uint32_t *perm = reinterpret_cast<uint32_t *>(keys + nq);
     k_order_keys<<<(nq + 255) / 256, 256, 0, st>>>(q.ip, q.t, q.v, nq, keys);
     SZ_CUDA(cudaGetLastError());
-    static bool attr = false;
-    if (!attr) {
-      SZ_CUDA(cudaFuncSetAttribute(k_order_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, kOrderChunk * 8));
-      attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    if ((rc = set_smem_limit_once(attr, (const void *)k_order_sort, kOrderChunk * 8))) return rc;
     k_order_sort<<<(nq + kOrderChunk - 1) / kOrderChunk, 1024, kOrderChunk * 8, st>>>(keys, nq, perm);
     SZ_CUDA(cudaGetLastError());
     a.perm = perm;

@@ -725,11 +725,9 @@ __global__ void __launch_bounds__(NW * 32, 1280 / (NW * 32))
 
 template <int G, int NW>
 int launch_t(const SearchArgs &a, size_t smem, uint32_t grid, cudaStream_t st) {
-  static bool configured = false;
-  if (!configured) {
-    SZ_CUDA(cudaFuncSetAttribute(k_search<G, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    configured = true;
-  }
+  static std::atomic<uint64_t> configured{0};
+  int rc = set_smem_limit_once(configured, (const void *)k_search<G, NW>, 200 * 1024);
+  if (rc) return rc;
   k_search<G, NW><<<grid, NW * 32, smem, st>>>(a);
   SZ_CUDA(cudaGetLastError());
   return SEISMIC_OK;

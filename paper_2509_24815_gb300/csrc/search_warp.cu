@@ -474,11 +474,9 @@ __global__ void __launch_bounds__(128, 5) k_search_warp(const SearchArgs a) {
 
 template <int G, int R>
 int launch_w(const SearchArgs &a, size_t smem, uint32_t grid, uint32_t wpb, cudaStream_t st) {
-  static bool configured = false;
-  if (!configured) {
-    SZ_CUDA(cudaFuncSetAttribute(k_search_warp<G, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    configured = true;
-  }
+  static std::atomic<uint64_t> configured{0};
+  int rc = set_smem_limit_once(configured, (const void *)k_search_warp<G, R>, 200 * 1024);
+  if (rc) return rc;
   k_search_warp<G, R><<<grid, wpb * 32, smem, st>>>(a);
   SZ_CUDA(cudaGetLastError());
   return SEISMIC_OK;

@@ -26,6 +26,19 @@ int cuda_fail(cudaError_t e, const char *what);
     if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
   } while (0)
 
+// Sets a kernel's dynamic shared-memory limit once per device (function
+// attributes belong to the device's context); safe from several host threads,
+// since setting it twice is harmless.
+inline int set_smem_limit_once(std::atomic<uint64_t> &done, const void *func, int bytes) {
+  int dev = 0;
+  SZ_CUDA(cudaGetDevice(&dev));
+  const uint64_t bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return SEISMIC_OK;
+  SZ_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done.fetch_or(bit, std::memory_order_release);
+  return SEISMIC_OK;
+}
+
 // ---------------------------------------------------------------- threads
 inline int hw_threads(int want) {
   int n = (int)std::thread::hardware_concurrency();
