@@ -312,7 +312,7 @@ def main():
     ap.add_argument("--cta-warps", type=int, default=0)
     ap.add_argument("--wave", type=int, default=16)
     ap.add_argument("--persistent", type=int, default=1)
-    ap.add_argument("--shape", type=int, default=1, help="1: CTA per query, 2: warp per query, 0: auto")
+    ap.add_argument("--shape", type=int, default=1, help="1 (or 0): CTA per query, 2: warp per query")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--learn-target", type=float, default=0.9)
