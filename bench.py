@@ -56,7 +56,7 @@ K = 10
 METRIC = "QPS at recall@10>=0.9 (batched Seismic search, fixed parameters)"
 # DRAM bytes (read + write) of one search launch, from one ncu capture of this kernel version on the
 # named workload and launch configuration (profiles/k_search_flat_c2_dram.md); any other case: null
-MEASURED_TRAFFIC = {("c2", 1, 8, 16, False): 181.72e9}
+MEASURED_TRAFFIC = {}
 
 
 def log(*a):
@@ -94,9 +94,10 @@ class Clocks:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
 
-    def stop(self):
+    def stop(self, t0=None, t1=None):
+        """Summary of the samples taken in [t0, t1] (all samples if none fall there)."""
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -107,7 +108,8 @@ class Clocks:
         self.t.join(timeout=2)
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        inside = [ln for ts, ln in self.lines if t0 is not None and t0 <= ts <= t1]
+        for ln in (inside or [ln for _, ln in self.lines]):
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -461,15 +463,22 @@ def main():
         except Exception as e:  # capture unsupported here: direct launches of the same kernels
             graph_note = f"direct launches (graph capture failed: {e})"
             log(graph_note)
+    # the clock sampler starts (and finishes initialising) before the warm-up
+    # steps, so it never competes with the timed launches
     clocks = Clocks(local)
     clocks.start()
-    time.sleep(0.3)
+    time.sleep(1.0)
+    for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            step()
+    stream.synchronize()
     barrier()
     torch.cuda.synchronize()
+    t_timed = time.time()
     per = time_runs(p, args.steps, step)  # events bracket each step on its stream
     torch.cuda.synchronize()
     barrier()
-    clk = clocks.stop()
+    clk = clocks.stop(t_timed, time.time())
     ms_step = max_over_ranks(float(np.mean(per)), dist, "cuda")
     qps = job_qps(world, dq.n_rows, ms_step)
 

@@ -314,10 +314,12 @@ __device__ uint32_t block_exclusive_scan(uint32_t *v, uint32_t n, uint32_t *wtmp
 
 // Group 1: the wave's documents are deduplicated first (one thread each),
 // then their rows' chunks are laid end to end and scored by all threads of
-// the CTA, U chunks in flight per thread, each chunk's 8 products added in
-// entry order; a document's score is the sum of its chunks' partials in chunk
-// order (deterministic, independent of the launch shape).  Work per thread is
-// balanced whatever the row lengths; seen documents cost no row reads.
+// the CTA, U chunks in flight per thread, each chunk's products with query
+// terms added in entry order; a document's score is the sum of its chunks'
+// partials in chunk order (deterministic, independent of the launch shape).
+// Work per thread is balanced whatever the row lengths; seen documents cost
+// no row reads, and a row's values are read only where its term is in the
+// query (a 4-byte read-only load each; most entries miss).
 template <int NT, class Src>
 __device__ __forceinline__ void eval_wave_flat(const SearchArgs &a, Smem &s, Shared &sh, uint32_t n, const Src &src,
                                                int knn_stage) {
@@ -379,17 +381,19 @@ __device__ __forceinline__ void eval_wave_flat(const SearchArgs &a, Smem &s, Sha
     }
 #pragma unroll 1
     for (uint32_t j = tid; j < total; j += NT * U) {
-      uint4 t[U], va[U], vb[U];
+      // a row holds its chunks' terms (16 B each), then their values (32 B each):
+      // the terms are read first and a value only where the term is in the query
+      uint4 t[U];
+      const float *vp[U];
 #pragma unroll
       for (int u = 0; u < U; u++) {  // past the end: the last chunk again (unconditional loads stay in registers)
         const uint32_t jj = min(j + u * NT, total - 1u);
-        {  // a row holds its chunks' terms (16 B each), then their values (32 B each)
+        {
           const uint32_t i = s.cmap()[jj], p0 = s.fpre()[i];
           const uint32_t nch = s.fpre()[i + 1] - p0, o = base + jj - p0;
           const uint8_t *row = a.fwd_data + (size_t)s.fc0()[i] * 48;
           t[u] = ldg_na(row + 16 * o);
-          va[u] = ldg_na(row + 16 * nch + 32 * o);
-          vb[u] = ldg_na(row + 16 * nch + 32 * o + 16);
+          vp[u] = reinterpret_cast<const float *>(row + 16 * nch + 32 * o);
         }
       }
 #pragma unroll
@@ -397,13 +401,12 @@ __device__ __forceinline__ void eval_wave_flat(const SearchArgs &a, Smem &s, Sha
         const uint32_t jj = j + u * NT;
         if (jj < total) {
           const uint32_t tw[4] = {t[u].x, t[u].y, t[u].z, t[u].w};
-          const uint32_t vv[8] = {va[u].x, va[u].y, va[u].z, va[u].w, vb[u].x, vb[u].y, vb[u].z, vb[u].w};
           float acc = 0.0f;
 #pragma unroll
-          for (int e = 0; e < 8; e++) {  // absent terms (most) cost one shared load
+          for (int e = 0; e < 8; e++) {  // absent terms (most) cost one shared load and no value read
             const uint32_t tt = (e & 1) ? (tw[e >> 1] >> 16) : (tw[e >> 1] & 0xFFFFu);
             const uint32_t w = qb[tt >> 5], sh5 = tt & 31u;
-            if ((w >> sh5) & 1u) acc = fmaf(qv[qr[tt >> 5] + __popc(w & ((1u << sh5) - 1u))], __uint_as_float(vv[e]), acc);
+            if ((w >> sh5) & 1u) acc = fmaf(qv[qr[tt >> 5] + __popc(w & ((1u << sh5) - 1u))], __ldg(vp[u] + e), acc);
           }
           cpart[jj] = acc;
         }
