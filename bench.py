@@ -313,7 +313,8 @@ def run_reference(args, w):
             "unit": "queries/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * float(np.median(cb["times_s"])), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w["desc"], "cut": cut, "heap_factor": hf},
+            "config": {"workload": w["desc"], "cut": cut, "heap_factor": hf, "k": K, "queries_per_step": queries.n_rows,
+                       "sample_per_step": min(w["cpu_sample"], queries.n_rows)},
             "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
             "e2e": {"value": cb["value"], "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
