@@ -55,7 +55,7 @@ RECALL_TARGET = 0.9
 K = 10
 METRIC = "QPS at recall@10>=0.9 (batched Seismic search, fixed parameters)"
 # DRAM bytes (read + write) of one search launch, from one ncu capture of this kernel version on the
-# named workload and launch configuration (profiles/k_search_flat_c2_dram.md); any other case: null
+# named workload and launch configuration; any other case: null
 MEASURED_TRAFFIC = {}
 
 

@@ -303,8 +303,11 @@ void seismic_server_destroy(seismic_server *srv);
  * seismic_search with the same results, and calls no cudaMalloc, cudaFree or
  * allocating library routine.
  *   - queries, ids_out and scores_out must be device buffers; params must set
- *     max_query_nnz; stats, learned parameters and work-queue ordering are not
- *     available here (queries run in input order; results are the same).
+ *     max_query_nnz.  Not available here: stats, learned parameters, the
+ *     warp-per-query shape (shape = 2 is refused with EINVAL), work-queue
+ *     ordering (`order` is ignored: queries run in input order, with the same
+ *     results) and `hash_slots` (ignored: the seen set is the bitmap in the
+ *     fixed array).
  *   - Working memory is one fixed 32 MiB device array inside the library,
  *     held by every GPU that loads it until the process exits: a 256-byte
  *     header (queue counter, error word, cleared on `stream` at each call)

@@ -216,7 +216,8 @@ def seismic_search(index: Index, queries, params: SearchParams | None = None, *,
     numpy (ids uint32, scores float32); DeviceCSR -> torch CUDA tensors (or the
     given ``ids_out``/``scores_out``).  ``stats=True`` also returns the
     per-query work counters (uint64 [nq, len(STATS)])."""
-    p = params if params is not None else search_params(**kw)
+    # a copy: the caller's struct is never written (a bound filled here would go stale on a larger batch)
+    p = SearchParams.from_buffer_copy(params) if params is not None else search_params(**kw)
     if isinstance(queries, DeviceCSR) and not p.max_query_nnz and queries.max_row_nnz:
         p.max_query_nnz = queries.max_row_nnz
     s, keep = _csr_struct(queries)
@@ -341,10 +342,11 @@ def seismic_search_noalloc(index: Index, queries: DeviceCSR, params: SearchParam
     """Search with no memory allocation (device queries and outputs, torch CUDA
     tensors); work memory is the library's fixed device array.  Enqueued on
     ``stream`` without waiting; calls that overlap on the GPU race."""
-    if not params.max_query_nnz:
-        params.max_query_nnz = queries.max_row_nnz
+    p = SearchParams.from_buffer_copy(params)  # the caller's struct is never written
+    if not p.max_query_nnz:
+        p.max_query_nnz = queries.max_row_nnz
     s, keep = _csr_struct(queries)
-    _check(_lib.seismic_search_noalloc(index.handle, ctypes.byref(s), ctypes.byref(params), ids_out.data_ptr(),
+    _check(_lib.seismic_search_noalloc(index.handle, ctypes.byref(s), ctypes.byref(p), ids_out.data_ptr(),
                                        scores_out.data_ptr(), _stream_ptr(stream)))
 
 

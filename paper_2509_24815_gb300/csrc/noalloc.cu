@@ -56,6 +56,8 @@ extern "C" int seismic_search_noalloc(seismic_index *ix, const seismic_csr *quer
   if (!p->exhaustive && !(p->heap_factor > 0.0f)) return fail(SEISMIC_EINVAL, "heap_factor must be > 0");
   if (p->hf_mode != 0 && p->hf_mode != 1) return fail(SEISMIC_EINVAL, "hf_mode must be 0 or 1");
   if (p->use_knn && ix->kappa == 0) return fail(SEISMIC_EINVAL, "use_knn: the index has no kappa-NN graph");
+  if (p->shape == 2) return fail(SEISMIC_EINVAL, "noalloc search: only the CTA-per-query shape (0 or 1)");
+  if (p->shape > 2) return fail(SEISMIC_EINVAL, "shape must be 0 (auto), 1 (CTA per query) or 2 (warp per query)");
   const uint32_t group = p->group ? p->group : 1, nw = p->cta_warps ? p->cta_warps : 8;
   if (!(group == 1 || group == 8 || group == 16 || group == 32) || !(nw == 4 || nw == 8 || nw == 16))
     return fail(SEISMIC_EINVAL, "noalloc search: group must be 1/8/16/32 and cta_warps 4/8/16");

@@ -51,7 +51,7 @@ def test_no_gpu_needed_for_error_paths(lib):
     assert rc == sz.EINVAL and "NULL" in sz.seismic_last_error()
 
 
-def test_struct_layouts_match_header():
+def test_struct_layouts_match_header(tmp_path):
     """Compile a tiny C program against the header and compare sizes/offsets."""
     import paper_2509_24815_gb300 as sz
     prog = r"""
@@ -66,8 +66,7 @@ int main(void){
  printf("%zu\n", offsetof(seismic_build_params, keep_block_summaries));
  return 0;}
 """
-    tmp = os.path.join(ROOT, "_build_layout_probe")
-    os.makedirs(tmp, exist_ok=True)
+    tmp = str(tmp_path)
     c = os.path.join(tmp, "p.c")
     exe = os.path.join(tmp, "p")
     open(c, "w").write(prog)

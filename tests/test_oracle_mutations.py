@@ -1,7 +1,7 @@
 """The oracle's pins catch the plausible mistakes: each case below plants one
-mistake in a copy of the oracle (on the CPU, in a scratch folder of the
-repository), rebuilds it and runs the pins in a fresh process; the run must
-fail.  A pin set that let one of them through would not pin the oracle."""
+mistake in a copy of the oracle (on the CPU, in pytest's temporary folder),
+rebuilds it and runs the pins in a fresh process; the run must fail.  A pin
+set that let one of them through would not pin the oracle."""
 import os
 import shutil
 import subprocess
@@ -10,7 +10,7 @@ import sys
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-SCRATCH = os.path.join(ROOT, "_mutants")
+PIN_FILES = ("tests/test_oracle_pins.py", "tests/test_oracle_mlp.py")
 
 MUTATIONS = [
     ("skip test flipped (Section 4.5)", "(rb[bi].r < c->hf * theta)", "(rb[bi].r > c->hf * theta)"),
@@ -37,40 +37,55 @@ MUTATIONS = [
      "ceil(((double)o->sval[used + i] - (double)lo) / (double)size)"),
     ("kappa-NN expansion reads the wrong graph row", "c->knn[(uint64_t)S[i] * c->kappa + e]",
      "c->knn[(uint64_t)(S[i] + 1) * c->kappa + e]"),
+    ("pair scoring keeps the previous query's terms",
+     "for (uint64_t p = qip[cur]; p < qip[cur + 1]; p++) qd[qt[p]] = 0.0;",
+     "for (uint64_t p = qip[cur]; p < qip[cur]; p++) qd[qt[p]] = 0.0;"),
+]
+
+# mistakes in the oracle MLP (oracle/mlp.py); each is a list of (old, new)
+# sites.  The first is shared by the forward pass and the gradient, so the
+# finite-difference pin alone would not see it.
+MLP_MUTATIONS = [
+    ("absolute value for ReLU in forward and gradient",
+     [("a1 = np.maximum(z1, 0.0)", "a1 = np.abs(z1)"), ("* (z1 > 0)", "* np.sign(z1)")]),
+    ("hidden layers without biases", [("z1 = x @ p[\"W1\"].T + p[\"b1\"]", "z1 = x @ p[\"W1\"].T")]),
 ]
 
 
-def run_pins(tag, old=None, new=None):
-    """Copies the oracle, generator and tests, plants old -> new in the
-    oracle's C source (if given), runs the pins; returns the pytest run."""
-    work = os.path.join(SCRATCH, tag)
-    shutil.rmtree(work, ignore_errors=True)
-    os.makedirs(work)
-    try:
-        for d in ("oracle", "synth", "tests"):
-            shutil.copytree(os.path.join(ROOT, d), os.path.join(work, d),
-                            ignore=shutil.ignore_patterns("*.so", "__pycache__", "*.tmp*"))
-        shutil.copy(os.path.join(ROOT, "pytest.ini"), work)
-        if old is not None:
-            src = os.path.join(work, "oracle", "oracle.c")
-            text = open(src).read()
-            assert text.count(old) == 1, "the mutation site moved"
-            with open(src, "w") as f:
-                f.write(text.replace(old, new))
-        return subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-q", "-x",
-                               "-p", "no:cacheprovider"], cwd=work, capture_output=True, text=True, timeout=900)
-    finally:
-        shutil.rmtree(work, ignore_errors=True)
+def run_pins(work, fname=None, sites=()):
+    """Copies the oracle, generator and tests into `work`, plants each
+    (old, new) site in oracle/<fname>, runs the pins; returns the pytest run."""
+    for d in ("oracle", "synth", "tests"):
+        shutil.copytree(os.path.join(ROOT, d), os.path.join(work, d),
+                        ignore=shutil.ignore_patterns("*.so", "__pycache__", "*.tmp*"))
+    shutil.copy(os.path.join(ROOT, "pytest.ini"), work)
+    if sites:
+        src = os.path.join(work, "oracle", fname)
+        text = open(src).read()
+        for old, new in sites:
+            assert text.count(old) >= 1, "the mutation site moved"
+            text = text.replace(old, new)
+        with open(src, "w") as f:
+            f.write(text)
+    return subprocess.run([sys.executable, "-m", "pytest", *PIN_FILES, "-q", "-x", "-p", "no:cacheprovider"],
+                          cwd=work, capture_output=True, text=True, timeout=900)
 
 
-def test_unchanged_copy_passes():
+def test_unchanged_copy_passes(tmp_path):
     """The harness itself: an unchanged copy passes every pin."""
-    r = run_pins("control")
+    r = run_pins(str(tmp_path))
     assert r.returncode == 0, r.stdout[-2000:]
 
 
 @pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
-def test_pins_catch_the_mistake(name, old, new):
-    r = run_pins(str(MUTATIONS.index((name, old, new))), old, new)
+def test_pins_catch_the_mistake(tmp_path, name, old, new):
+    r = run_pins(str(tmp_path), "oracle.c", [(old, new)])
+    assert r.returncode != 0, f"{name}: every pin passed\n{r.stdout[-2000:]}"
+    assert "failed" in r.stdout, r.stdout[-2000:]
+
+
+@pytest.mark.parametrize("name,sites", MLP_MUTATIONS, ids=[m[0] for m in MLP_MUTATIONS])
+def test_pins_catch_the_mlp_mistake(tmp_path, name, sites):
+    r = run_pins(str(tmp_path), "mlp.py", sites)
     assert r.returncode != 0, f"{name}: every pin passed\n{r.stdout[-2000:]}"
     assert "failed" in r.stdout, r.stdout[-2000:]

@@ -419,3 +419,26 @@ def test_recall_definition():
     assert r[0] == 0.5
     r = oracle.recall_at_k(docs, Q, np.array([[0, NONE]], dtype=np.uint32), es, 2)
     assert r[0] == 0.5
+
+
+def test_pair_dots_matches_numpy_on_interleaved_queries():
+    """or_pair_dots, the checker behind every GPU score and every recall, against
+    a dense numpy product (textbook inner product, fp64) on several queries
+    whose pairs come unsorted and interleaved (a query revisited after others),
+    with repeated pairs, mixed-sign values and ids past the collection (-inf)."""
+    rng = np.random.default_rng(17)
+    docs = _random_csr(rng, 60, 90, 1, 25, neg=True)
+    queries = _random_csr(rng, 9, 90, 1, 30, neg=True)
+    D, Q = docs.to_dense(), queries.to_dense()
+    qi = rng.integers(0, queries.n_rows, size=400).astype(np.uint64)
+    di = rng.integers(0, docs.n_rows + 5, size=400).astype(np.uint32)  # a few ids past the end
+    qi[:6] = [3, 0, 3, 8, 8, 0]
+    di[:6] = [7, 7, 7, 2, 2, 61]
+    got = oracle.pair_dots(docs, queries, qi, di)
+    q64, d64 = qi.astype(np.int64), di.astype(np.int64)
+    ok = d64 < docs.n_rows
+    want = np.full(len(qi), -np.inf)
+    want[ok] = np.einsum("ij,ij->i", Q[q64[ok]], D[d64[ok]])
+    assert np.all(np.isneginf(got[~ok]))
+    np.testing.assert_allclose(got[ok], want[ok], rtol=1e-12, atol=1e-12)
+    assert got[0] == got[2]  # the same pair, with another query scored in between
