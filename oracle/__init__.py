@@ -57,6 +57,7 @@ def _load():
             lib.or_list_sizes.argtypes = [vp, u32, vp]
             lib.or_list_get.argtypes = [vp, u32] + [vp] * 13
             lib.or_knn_exact.argtypes = [vp, vp, vp, u64, u32, u32, ci, vp]
+            lib.or_knn_refine.argtypes = [vp, vp, vp, u64, u32, vp, u32, ci, vp]
             lib.or_search.argtypes = [vp, vp, vp, vp, u64, vp, vp, vp, u64, u32, u32, dbl, dbl, ci, ci,
                                       vp, u32, ci, vp, vp, vp, vp]
             lib.or_block_scores.argtypes = [vp, vp, vp, u32, u32, vp]
@@ -193,6 +194,19 @@ def knn_exact(docs, kappa: int, threads=None):
     out = np.empty((docs.n_rows, kappa), dtype=np.uint32)
     lib.or_knn_exact(_p(d_[0]), _p(d_[1]), _p(d_[2]), docs.n_rows, docs.dim, kappa, _threads(threads),
                      _p(out))
+    return out
+
+
+def knn_refine(docs, knn, threads=None):
+    """One neighbour-of-neighbour pass: the new N(u) is the kappa best v != u of
+    N(u) u N(N(u)) by (<u,v> desc, id asc), fp64 (the expansion step of query
+    processing applied to the graph itself)."""
+    lib = _load()
+    d_ = _csr_args(docs)
+    kn = np.ascontiguousarray(knn, dtype=np.uint32)
+    out = np.empty_like(kn)
+    lib.or_knn_refine(_p(d_[0]), _p(d_[1]), _p(d_[2]), docs.n_rows, docs.dim, _p(kn), kn.shape[1],
+                      _threads(threads), _p(out))
     return out
 
 

@@ -16,6 +16,8 @@
  *                      gamma-MSS of the summary and 8-bit scalar quantisation
  *                      (Section 4.1.3).
  *   or_knn_exact    -- Eq. "knn-graph" (Section 4.3), computed exactly.
+ *   or_knn_refine   -- one neighbour-of-neighbour pass over a graph: the
+ *                      expansion step of Section 4.5 applied to N(u) itself.
  *   or_search       -- Algorithm "Query processing with Seismic" (Section 4.5).
  *
  * Readings where the paper is silent or inconsistent (all listed in the
@@ -652,6 +654,73 @@ int or_knn_exact(const uint64_t *dip, const uint16_t *dt, const float *dv, uint6
   for (int i = 0; i < threads; i++) { free(c.acc[i]); free(c.stamp[i]); free(c.heap[i]); }
   free(c.acc); free(c.stamp); free(c.heap);
   inv_free(&L);
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* One neighbour-of-neighbour pass over a kappa-NN graph (not a step of the
+ * paper; its Section 4.3 builds N(u) approximately with the method itself,
+ * and this pass applies that method's expansion step -- candidates are the
+ * union of the neighbour lists of a set, Algorithm "Query processing with
+ * Seismic" -- to the graph): for every u, the candidates are
+ * C(u) = (N(u) u N(N(u))) \ {u}, missing entries dropped, and the new N(u)
+ * is the kappa best of C(u) by (<u,v> desc, id asc) in fp64, padded with
+ * NONE_ID.  Reads `in` only, writes `out` (they must not overlap). */
+typedef struct {
+  const csr_t *D;
+  const uint32_t *in;
+  uint32_t kappa;
+  uint32_t *out;
+  double **qd;
+  uint32_t **stamp;
+  ent_t **heap;
+} rf_ctx;
+
+static void refine_one(void *vc, int64_t ui, int tid) {
+  rf_ctx *c = (rf_ctx *)vc;
+  const csr_t *D = c->D;
+  double *qd = c->qd[tid];
+  uint32_t *st = c->stamp[tid];
+  const uint32_t mark = (uint32_t)ui + 1, K = c->kappa;
+  topk_t h = {c->heap[tid], 0, K};
+  for (uint64_t p = D->indptr[ui]; p < D->indptr[ui + 1]; p++) qd[D->terms[p]] = (double)D->vals[p];
+  st[ui] = mark; /* u itself is never a candidate */
+  for (uint32_t i = 0; i <= K; i++) {
+    /* i = 0: u's own list; i >= 1: the list of its (i-1)-th neighbour */
+    uint32_t src = (uint32_t)ui;
+    if (i > 0) {
+      src = c->in[(uint64_t)ui * K + (i - 1)];
+      if (src == NONE_ID) continue;
+    }
+    for (uint32_t e = 0; e < K; e++) {
+      uint32_t v = c->in[(uint64_t)src * K + e];
+      if (v == NONE_ID || st[v] == mark) continue;
+      st[v] = mark;
+      double s = 0.0;
+      for (uint64_t p = D->indptr[v]; p < D->indptr[v + 1]; p++) s += qd[D->terms[p]] * (double)D->vals[p];
+      offer(&h, s, v);
+    }
+  }
+  for (uint64_t p = D->indptr[ui]; p < D->indptr[ui + 1]; p++) qd[D->terms[p]] = 0.0;
+  for (uint32_t j = 0; j < K; j++) c->out[(uint64_t)ui * K + j] = j < h.n ? h.e[j].id : NONE_ID;
+}
+
+int or_knn_refine(const uint64_t *dip, const uint16_t *dt, const float *dv, uint64_t nd, uint32_t d,
+                  const uint32_t *in, uint32_t kappa, int threads, uint32_t *out) {
+  csr_t D = mk(dip, dt, dv, nd, d);
+  if (threads < 1) threads = 1;
+  rf_ctx c = {&D, in, kappa, out, NULL, NULL, NULL};
+  c.qd = (double **)calloc(threads, sizeof(void *));
+  c.stamp = (uint32_t **)calloc(threads, sizeof(void *));
+  c.heap = (ent_t **)calloc(threads, sizeof(void *));
+  for (int i = 0; i < threads; i++) {
+    c.qd[i] = (double *)calloc(d ? d : 1, sizeof(double));
+    c.stamp[i] = (uint32_t *)calloc(nd ? nd : 1, sizeof(uint32_t));
+    c.heap[i] = (ent_t *)malloc(sizeof(ent_t) * (kappa + 1));
+  }
+  pfor((int64_t)nd, threads, refine_one, &c);
+  for (int i = 0; i < threads; i++) { free(c.qd[i]); free(c.stamp[i]); free(c.heap[i]); }
+  free(c.qd); free(c.stamp); free(c.heap);
   return 0;
 }
 

@@ -37,6 +37,10 @@ MUTATIONS = [
      "ceil(((double)o->sval[used + i] - (double)lo) / (double)size)"),
     ("kappa-NN expansion reads the wrong graph row", "c->knn[(uint64_t)S[i] * c->kappa + e]",
      "c->knn[(uint64_t)(S[i] + 1) * c->kappa + e]"),
+    ("graph refinement skips u's own list", "for (uint32_t i = 0; i <= K; i++) {",
+     "for (uint32_t i = 1; i <= K; i++) {"),
+    ("graph refinement keeps u among its own candidates", "st[ui] = mark; /* u itself is never a candidate */",
+     "st[ui] = 0; /* u itself is never a candidate */"),
     ("pair scoring keeps the previous query's terms",
      "for (uint64_t p = qip[cur]; p < qip[cur + 1]; p++) qd[qt[p]] = 0.0;",
      "for (uint64_t p = qip[cur]; p < qip[cur]; p++) qd[qt[p]] = 0.0;"),

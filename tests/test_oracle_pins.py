@@ -276,6 +276,48 @@ def test_knn_exact_matches_numpy(small):
         np.testing.assert_array_equal(nb[u], _np_topk(S[u], 5, allowed))
 
 
+def test_knn_refine_brute_force(small):
+    """One neighbour-of-neighbour pass against dense numpy on a tiny case: the
+    candidates of u are its list and its neighbours' lists (self loops and
+    missing entries in the input included), u excluded; the new list is their
+    kappa best by (score desc, id asc)."""
+    docs, _ = small
+    sub = docs.slice(0, 120)
+    rng = np.random.default_rng(9)
+    g = rng.integers(0, sub.n_rows, size=(sub.n_rows, 4)).astype(np.uint32)
+    g[rng.random(g.shape) < 0.15] = NONE
+    g[3, 0] = 3  # a self loop in the input
+    out = oracle.knn_refine(sub, g, threads=3)
+    S = sub.to_dense() @ sub.to_dense().T
+    for u in range(sub.n_rows):
+        cand = set(int(x) for x in g[u] if x != NONE)
+        for v in list(cand):
+            cand.update(int(x) for x in g[v] if x != NONE)
+        cand.discard(u)
+        allowed = np.zeros(sub.n_rows, bool)
+        allowed[list(cand)] = True
+        np.testing.assert_array_equal(out[u], _np_topk(S[u], 4, allowed), err_msg=f"row {u}")
+
+
+def test_knn_refine_keeps_the_exact_graph_and_improves_others(small):
+    """The exact graph is a fixed point (its lists are among the candidates and
+    beat every other document); on any other graph each rank's score never
+    drops (the old list is among the candidates)."""
+    docs, _ = small
+    sub = docs.slice(0, 400)
+    exact = oracle.knn_exact(sub, 6, threads=4)
+    np.testing.assert_array_equal(oracle.knn_refine(sub, exact, threads=4), exact)
+    rng = np.random.default_rng(2)
+    g = np.stack([rng.permutation(np.delete(np.arange(sub.n_rows), u))[:6] for u in range(sub.n_rows)])
+    g = g.astype(np.uint32)
+    S = sub.to_dense() @ sub.to_dense().T
+    g2 = oracle.knn_refine(sub, g, threads=4)
+    old = np.sort(np.take_along_axis(S, g.astype(np.int64), 1), axis=1)[:, ::-1]
+    new = np.take_along_axis(S, g2.astype(np.int64), 1)
+    assert np.all(new >= old - 1e-12)
+    assert (new > old + 1e-12).any()
+
+
 # ---------------------------------------------------------------- search
 def test_exhaustive_equals_brute_force_on_positive_scores(small):
     """With every query term traversed and unpruned lists, exhaustive Seismic is
