@@ -76,6 +76,13 @@ typedef struct {
   int32_t threads;       /* host threads used by the build; 0 = all */
   int32_t keep_block_summaries; /* 1: also keep the block-major summary arrays (SEISMIC_X_SUM_*);
                                    search reads only the term-major copy */
+  int32_t values_fp16;   /* 1: 16-bit forward values (the 16-bit setup of Section 5.4): every
+                            document value is rounded to the nearest fp16 (ties to even) on
+                            input, and the whole index -- lists, blocks, summaries, exact search --
+                            is built from that rounded collection, so results equal those of an
+                            fp32 index of the rounded values.  Rows shrink from 6 to 4 bytes per
+                            entry.  A value beyond the fp16 range (|v| > 65504) is EINVAL; one that
+                            rounds to 0 is dropped like an explicit zero */
 } seismic_build_params;
 
 /* Query processing (Algorithm "Query processing with Seismic", Section 4.5). */
@@ -115,10 +122,15 @@ typedef struct {
   uint32_t order;        /* persistent launches: 0 (default) runs queries grouped by their
                             largest term, so queries reading the same lists share L2; 1 runs
                             them in input order.  Results do not depend on it */
+  uint32_t ctas_per_sm;  /* CTA shape: 0 or 5 = the default build of the kernel (48 registers, 5
+                            CTAs of 8 warps per SM); 6 = a build capped at 40 registers so that 6
+                            share an SM (group 1 and 8 warps only).  A speed knob: same results */
 } seismic_search_params;
 
 /* Per-query work counters written by seismic_search when `stats` is non-NULL:
- * uint64_t stats[n_queries][SEISMIC_STATS_N]. */
+ * uint64_t stats[n_queries][SEISMIC_STATS_N].  The last two are device
+ * timestamps (the GPU's global nanosecond timer), not counts: when the query's
+ * CTA (or warp) took it up and when it wrote its results. */
 enum {
   SEISMIC_ST_LISTS = 0,          /* posting lists traversed */
   SEISMIC_ST_BLOCKS_SCORED,      /* blocks whose summary was scored */
@@ -132,6 +144,8 @@ enum {
   SEISMIC_ST_DIR_LOOKUPS,        /* summary directory entries read */
   SEISMIC_ST_BLOCK_DOCS,         /* block member ids read */
   SEISMIC_ST_QUERY_NNZ,          /* query entries read */
+  SEISMIC_ST_T_START,            /* ns: the query was taken up */
+  SEISMIC_ST_T_END,              /* ns: its results were written */
   SEISMIC_STATS_N
 };
 
@@ -141,6 +155,10 @@ typedef struct {
   uint32_t dim, kappa;
   int32_t quantize_u8, has_full_lists, has_mlp;
   uint64_t device_bytes;  /* device memory held by the index */
+  int32_t values_fp16;    /* the forward values are 16-bit */
+  uint32_t knn_bits;      /* bits per stored kappa-NN id: floor(log2(n_docs - 1)) + 1 (Section 4.3),
+                             one more when n_docs is a power of two (the missing-neighbour code) */
+  uint64_t knn_bytes;     /* device bytes of the packed graph */
 } seismic_index_info;
 
 /* Builds an index from `docs` (host or device CSR) on the current CUDA
@@ -174,6 +192,9 @@ int seismic_search_exact(seismic_index *index, const seismic_csr *queries, uint3
 
 /* Installs a kappa-NN graph (Eq. "knn-graph", Section 4.3): nbrs[n_docs *
  * kappa] row-major, SEISMIC_NONE_ID for missing neighbours; host or device.
+ * The index stores each id in floor(log2(n_docs - 1)) + 1 bits, the cost the
+ * paper gives for the graph (Section 4.3), packed back to back (one bit more
+ * when n_docs is a power of two, to leave a code for a missing neighbour).
  * Replaces any previous graph.  Errors: EINVAL (size mismatch, id out of
  * range), ENOMEM, ECUDA. */
 int seismic_set_knn(seismic_index *index, const uint32_t *nbrs, uint64_t n_docs, uint32_t kappa,
@@ -185,7 +206,19 @@ int seismic_set_knn(seismic_index *index, const uint32_t *nbrs, uint64_t n_docs,
  * removed).  Synchronous. */
 int seismic_build_knn(seismic_index *index, uint32_t kappa, const seismic_search_params *params);
 
-/* Copies the graph to the host: nbrs[n_docs * kappa]. */
+/* Improves the installed graph by `rounds` neighbour-of-neighbour passes (not
+ * a step of the paper: its Section 4.3 builds the graph approximately with
+ * Seismic itself, and a pass applies Seismic's expansion step -- the union of
+ * the neighbour lists of a set -- to the graph): in a round every document u
+ * is scored exactly against the documents of N(u) and of N(v) for v in N(u),
+ * and N(u) becomes the kappa best of them other than u, by (score desc, id
+ * asc).  A round reads only the graph from before it, so a row never gets
+ * worse and the exact graph is a fixed point.  `params` (may be NULL) only
+ * chooses the launch configuration (group, cta_warps, no_prefetch); the rest
+ * is fixed.  Synchronous.  Errors: EINVAL (no graph), ENOMEM, ECUDA. */
+int seismic_refine_knn(seismic_index *index, uint32_t rounds, const seismic_search_params *params);
+
+/* Copies the graph to the host, unpacked: nbrs[n_docs * kappa]. */
 int seismic_get_knn(const seismic_index *index, uint32_t *nbrs, uint64_t cap_entries);
 
 /* Versioned little-endian file of the whole index (and graph and MLP).

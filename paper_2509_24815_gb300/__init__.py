@@ -26,7 +26,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 NONE_ID = 0xFFFFFFFF
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUDGET, EIO = 0, -1, -2, -3, -4, -5, -6
 STATS = ("lists", "blocks_scored", "blocks_evaluated", "blocks_skipped", "docs", "doc_nnz", "knn_docs",
-         "summary_entries", "knn_nnz", "dir_lookups", "block_docs", "query_nnz")
+         "summary_entries", "knn_nnz", "dir_lookups", "block_docs", "query_nnz", "t_start_ns", "t_end_ns")
 EXPORTS = ("list_ptr", "list_doc", "blk_ptr", "bdoc_ptr", "bdoc", "blk_m", "blk_size", "sum_ptr", "sum_term",
            "sum_val", "sum_code", "cent")
 _EXPORT_DT = dict(list_ptr=np.uint32, list_doc=np.uint32, blk_ptr=np.uint32, bdoc_ptr=np.uint32, bdoc=np.uint32,
@@ -50,7 +50,7 @@ class BuildParams(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_uint32), ("beta", ctypes.c_uint32), ("alpha", ctypes.c_double),
                 ("quantize_u8", ctypes.c_int32), ("seed", ctypes.c_uint64), ("lambda_frac", ctypes.c_double),
                 ("beta_frac", ctypes.c_double), ("keep_full_lists", ctypes.c_int32), ("threads", ctypes.c_int32),
-                ("keep_block_summaries", ctypes.c_int32)]
+                ("keep_block_summaries", ctypes.c_int32), ("values_fp16", ctypes.c_int32)]
 
 
 class SearchParams(ctypes.Structure):
@@ -59,14 +59,15 @@ class SearchParams(ctypes.Structure):
                 ("use_knn", ctypes.c_int32), ("learned", ctypes.c_int32), ("wave", ctypes.c_uint32),
                 ("group", ctypes.c_uint32), ("cta_warps", ctypes.c_uint32), ("persistent", ctypes.c_uint32),
                 ("max_query_nnz", ctypes.c_uint32), ("hash_slots", ctypes.c_uint32), ("shape", ctypes.c_uint32),
-                ("no_prefetch", ctypes.c_int32), ("order", ctypes.c_uint32)]
+                ("no_prefetch", ctypes.c_int32), ("order", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32)]
 
 
 class IndexInfo(ctypes.Structure):
     _fields_ = [("n_docs", ctypes.c_uint64), ("nnz", ctypes.c_uint64), ("n_postings", ctypes.c_uint64),
                 ("n_blocks", ctypes.c_uint64), ("n_summary_entries", ctypes.c_uint64), ("dim", ctypes.c_uint32),
                 ("kappa", ctypes.c_uint32), ("quantize_u8", ctypes.c_int32), ("has_full_lists", ctypes.c_int32),
-                ("has_mlp", ctypes.c_int32), ("device_bytes", ctypes.c_uint64)]
+                ("has_mlp", ctypes.c_int32), ("device_bytes", ctypes.c_uint64), ("values_fp16", ctypes.c_int32),
+                ("knn_bits", ctypes.c_uint32), ("knn_bytes", ctypes.c_uint64)]
 
 
 class ServerParams(ctypes.Structure):
@@ -83,6 +84,7 @@ _SIGS = {
     "seismic_set_knn": ([_vp, _vp, _u64, _u32, _i32], ctypes.c_int),
     "seismic_build_knn": ([_vp, _u32, _P(SearchParams)], ctypes.c_int),
     "seismic_get_knn": ([_vp, _vp, _u64], ctypes.c_int),
+    "seismic_refine_knn": ([_vp, _u32, _P(SearchParams)], ctypes.c_int),
     "seismic_save": ([_vp, ctypes.c_char_p], ctypes.c_int),
     "seismic_load": ([ctypes.c_char_p, _P(_vp)], ctypes.c_int),
     "seismic_info": ([_vp, _P(IndexInfo)], ctypes.c_int),
@@ -191,11 +193,13 @@ class Index:
 
 
 def seismic_build(docs, lambda_=2000, beta=100, alpha=0.4, quantize_u8=False, seed=0, lambda_frac=0.0,
-                  beta_frac=0.0, keep_full_lists=False, threads=0, keep_block_summaries=False) -> Index:
+                  beta_frac=0.0, keep_full_lists=False, threads=0, keep_block_summaries=False,
+                  values_fp16=False) -> Index:
     """Algorithm "Indexing with Seismic" on the current CUDA device."""
     s, keep = _csr_struct(docs)
     p = BuildParams(int(lambda_), int(beta), float(alpha), int(bool(quantize_u8)), int(seed), float(lambda_frac),
-                    float(beta_frac), int(bool(keep_full_lists)), int(threads), int(bool(keep_block_summaries)))
+                    float(beta_frac), int(bool(keep_full_lists)), int(threads), int(bool(keep_block_summaries)),
+                    int(bool(values_fp16)))
     h = ctypes.c_void_p()
     _check(_lib.seismic_build(ctypes.byref(s), ctypes.byref(p), ctypes.byref(h)))
     return Index(h.value)
@@ -203,11 +207,11 @@ def seismic_build(docs, lambda_=2000, beta=100, alpha=0.4, quantize_u8=False, se
 
 def search_params(k=10, cut=10, heap_factor=0.8, hf_mode=0, exhaustive=False, alpha_q=0.0, use_knn=False,
                   learned=False, wave=1, group=0, cta_warps=0, persistent=False, max_query_nnz=0,
-                  hash_slots=0, shape=0, no_prefetch=False, order=0) -> SearchParams:
+                  hash_slots=0, shape=0, no_prefetch=False, order=0, ctas_per_sm=0) -> SearchParams:
     return SearchParams(int(k), int(cut), float(heap_factor), int(hf_mode), int(bool(exhaustive)), float(alpha_q),
                         int(bool(use_knn)), int(bool(learned)), int(wave), int(group), int(cta_warps),
                         int(bool(persistent)), int(max_query_nnz), int(hash_slots), int(shape),
-                        int(bool(no_prefetch)), int(order))
+                        int(bool(no_prefetch)), int(order), int(ctas_per_sm))
 
 
 def seismic_search(index: Index, queries, params: SearchParams | None = None, *, ids_out=None, scores_out=None,
@@ -276,6 +280,12 @@ def seismic_build_knn(index: Index, kappa: int, params: SearchParams | None = No
     else:
         p = params if params is not None else search_params()
         _check(_lib.seismic_build_knn(index.handle, kappa, ctypes.byref(p)))
+
+
+def seismic_refine_knn(index: Index, rounds: int = 1, params: SearchParams | None = None):
+    """Neighbour-of-neighbour passes over the installed graph: each row becomes
+    the kappa best of the document's list and its neighbours' lists."""
+    _check(_lib.seismic_refine_knn(index.handle, int(rounds), ctypes.byref(params) if params is not None else None))
 
 
 def seismic_get_knn(index: Index) -> np.ndarray:

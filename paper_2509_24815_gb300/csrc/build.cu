@@ -7,8 +7,13 @@
 // quantisation (Section 4.1.3), and the term-major summary layout.
 // Device: the shallow k-means assignment (Section 4.1.2), which dominates the
 // build: every list member against every centroid of its list.
+#include <cuda_fp16.h>
+
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <memory>
 
 #include "seismic_impl.h"
@@ -26,7 +31,11 @@ struct HostCsr {
 };
 
 // Copies `m` to host (if needed), validates it and drops explicit zeros.
-int fetch_docs(const seismic_csr *m, HostCsr &h) {
+// With fp16 = 1 every value is first rounded to the nearest fp16 (ties to
+// even): the index then stores, and search scores, that rounded collection
+// (the 16-bit value setup of Section 5.4); a value that rounds to 0 is
+// dropped like an explicit zero, one beyond the fp16 range is refused.
+int fetch_docs(const seismic_csr *m, HostCsr &h, int fp16) {
   if (!m || !m->indptr || m->n_rows == 0) return fail(SEISMIC_EINVAL, "documents: empty or NULL CSR");
   if (m->dim == 0 || m->dim > 65535) return fail(SEISMIC_EINVAL, "documents: dim must be in 1..65535");
   if (m->n_rows >= 0xFFFFFFFFull) return fail(SEISMIC_EINVAL, "documents: more than 2^32-2 rows");
@@ -59,10 +68,15 @@ int fetch_docs(const seismic_csr *m, HostCsr &h) {
   h.n = m->n_rows;
   h.d = m->dim;
   h.ip.assign(h.n + 1, 0);
+  auto value = [&](uint64_t p) { return fp16 ? __half2float(__float2half_rn(vp[p])) : vp[p]; };
+  if (fp16)
+    for (uint64_t p = 0; p < ipp[h.n]; p++)
+      if (std::isinf(value(p)))
+        return fail(SEISMIC_EINVAL, "documents: a value exceeds the fp16 range (|v| > 65504)");
   uint64_t nnz = 0;
   for (uint64_t i = 0; i < h.n; i++) {
     uint64_t c = 0;
-    for (uint64_t p = ipp[i]; p < ipp[i + 1]; p++) c += vp[p] != 0.0f;
+    for (uint64_t p = ipp[i]; p < ipp[i + 1]; p++) c += value(p) != 0.0f;
     if (c > kMaxRowNnzBuild)
       return fail(SEISMIC_EINVAL, "documents: a row has more than " + std::to_string(kMaxRowNnzBuild) +
                                       " nonzeros");
@@ -72,14 +86,28 @@ int fetch_docs(const seismic_csr *m, HostCsr &h) {
   h.t.resize(nnz);
   h.v.resize(nnz);
   for (uint64_t i = 0, o = 0; i < h.n; i++)
-    for (uint64_t p = ipp[i]; p < ipp[i + 1]; p++)
-      if (vp[p] != 0.0f) {
+    for (uint64_t p = ipp[i]; p < ipp[i + 1]; p++) {
+      const float v = value(p);
+      if (v != 0.0f) {
         h.t[o] = tp[p];
-        h.v[o] = vp[p];
+        h.v[o] = v;
         o++;
       }
+    }
   return SEISMIC_OK;
 }
+
+// Phase timings of a build, printed to stderr when SEISMIC_BUILD_TRACE=1.
+struct PhaseTimer {
+  bool on = std::getenv("SEISMIC_BUILD_TRACE") && std::getenv("SEISMIC_BUILD_TRACE")[0] == '1';
+  std::chrono::steady_clock::time_point t = std::chrono::steady_clock::now();
+  void mark(const char *what) {
+    if (!on) return;
+    const auto now = std::chrono::steady_clock::now();
+    std::fprintf(stderr, "seismic build: %-28s %8.2f s\n", what, std::chrono::duration<double>(now - t).count());
+    t = now;
+  }
+};
 
 uint64_t splitmix64_next(uint64_t &state) {
   uint64_t z = (state += 0x9E3779B97F4A7C15ull);
@@ -312,10 +340,10 @@ int validate_host_csr(const seismic_csr *m, const char *what, uint32_t dim_expec
 }
 
 uint64_t device_bytes(const seismic_index *ix) {
-  const DevBuf *b[] = {&ix->fwd_cptr, &ix->fwd_data, &ix->fwd_nnz, &ix->list_ptr, &ix->list_doc, &ix->cent,
+  const DevBuf *b[] = {&ix->fwd_row, &ix->fwd_data, &ix->fwd_nnz, &ix->list_ptr, &ix->list_doc, &ix->cent,
                        &ix->blk_ptr, &ix->bdoc_ptr, &ix->bdoc, &ix->bdoc_row, &ix->blk_m, &ix->blk_size, &ix->sum_ptr,
-                       &ix->sum_term, &ix->sum_val, &ix->sum_code, &ix->sdir, &ix->scol_blk, &ix->scol_code,
-                       &ix->scol_val, &ix->full_ptr, &ix->full_doc, &ix->full_val, &ix->knn, &ix->mlp};
+                       &ix->sum_term, &ix->sum_val, &ix->sum_code, &ix->sbm, &ix->scptr, &ix->scol_blk,
+                       &ix->scol_code, &ix->scol_val, &ix->full_ptr, &ix->full_doc, &ix->full_val, &ix->knn, &ix->mlp};
   uint64_t s = 0;
   for (auto *x : b) s += x->bytes;
   return s;
@@ -327,8 +355,11 @@ int build_index(const seismic_csr *docs, const seismic_build_params *bp, seismic
   if (bp->beta == 0 && !(bp->beta_frac > 0.0)) return fail(SEISMIC_EINVAL, "beta must be >= 1");
   if (bp->lambda_frac < 0.0 || bp->lambda_frac > 1.0 || bp->beta_frac < 0.0 || bp->beta_frac > 1.0)
     return fail(SEISMIC_EINVAL, "lambda_frac / beta_frac must be in [0, 1]");
+  if (bp->values_fp16 != 0 && bp->values_fp16 != 1) return fail(SEISMIC_EINVAL, "values_fp16 must be 0 or 1");
+  const int fp16 = bp->values_fp16;
+  PhaseTimer timer;
   HostCsr D;
-  int rc = fetch_docs(docs, D);
+  int rc = fetch_docs(docs, D, fp16);
   if (rc) return rc;
   const int T = hw_threads(bp->threads);
   const uint32_t d = D.d;
@@ -339,33 +370,44 @@ int build_index(const seismic_csr *docs, const seismic_build_params *bp, seismic
   ix->nnz = D.ip.back();
   ix->bp = *bp;
 
-  // ---- forward index, padded 8-entry chunks
-  std::vector<uint32_t> cptr(D.n + 1, 0);
+  timer.mark("input");
+  // ---- forward index: rows of 8-entry chunks in sector-aligned records
+  std::vector<uint64_t> frow(D.n);  // first unit | chunks << 32
   {
     std::vector<uint16_t> rnnz(D.n);
+    uint64_t units = 0;
     for (uint64_t i = 0; i < D.n; i++) {
-      uint64_t n = D.ip[i + 1] - D.ip[i];
+      const uint64_t n = D.ip[i + 1] - D.ip[i];
+      const uint32_t nch = (uint32_t)((n + kChunk - 1) / kChunk);
       rnnz[i] = (uint16_t)n;
-      uint64_t c = cptr[i] + (n + kChunk - 1) / kChunk;
-      if (c > 0xFFFFFFFFull) return fail(SEISMIC_EINVAL, "forward index exceeds 2^32 chunks");
-      cptr[i + 1] = (uint32_t)c;
+      frow[i] = units | ((uint64_t)nch << 32);
+      units += row_units(nch, fp16);
+      if (units > 0xFFFFFFFFull) return fail(SEISMIC_EINVAL, "forward index exceeds 2^32 32-byte units");
     }
-    std::vector<uint8_t> data((size_t)cptr[D.n] * kChunkBytes, 0);
+    std::vector<uint8_t> data((size_t)units * kUnitBytes, 0);
     parallel_for((int64_t)D.n, T, [&](int64_t i, int) {
-      uint64_t n = D.ip[i + 1] - D.ip[i];
-      uint32_t P = (cptr[i + 1] - cptr[i]) * kChunk;
-      uint8_t *rec = data.data() + (size_t)cptr[i] * kChunkBytes;
-      uint16_t *tt = reinterpret_cast<uint16_t *>(rec);
-      float *vv = reinterpret_cast<float *>(rec + 2 * (size_t)P);
+      const uint64_t n = D.ip[i + 1] - D.ip[i];
+      const uint32_t nch = (uint32_t)(frow[i] >> 32);
+      uint8_t *rec = data.data() + (size_t)(uint32_t)frow[i] * kUnitBytes;
       for (uint64_t p = 0; p < n; p++) {
-        tt[p] = D.t[D.ip[i] + p];
-        vv[p] = D.v[D.ip[i] + p];
+        const uint64_t o = p / kChunk, e = p % kChunk;
+        const uint16_t t = D.t[D.ip[i] + p];
+        const float v = D.v[D.ip[i] + p];
+        if (fp16) {
+          std::memcpy(rec + o * kUnitBytes + 2 * e, &t, 2);
+          const __half hv = __float2half_rn(v);  // exact: v is already an fp16 value
+          std::memcpy(rec + o * kUnitBytes + 16 + 2 * e, &hv, 2);
+        } else {
+          std::memcpy(rec + 2 * p, &t, 2);
+          std::memcpy(rec + (size_t)kUnitBytes * ((nch + 1) / 2) + 4 * p, &v, 4);
+        }
       }
     });
-    if ((rc = upload(ix->fwd_cptr, cptr)) || (rc = upload(ix->fwd_data, data)) || (rc = upload(ix->fwd_nnz, rnnz)))
+    if ((rc = upload(ix->fwd_row, frow)) || (rc = upload(ix->fwd_data, data)) || (rc = upload(ix->fwd_nnz, rnnz)))
       return rc;
   }
 
+  timer.mark("forward index");
   // ---- full inverted lists (ascending doc ids)
   std::vector<uint64_t> fptr(d + 1, 0);
   std::vector<uint32_t> fdoc(ix->nnz);
@@ -389,6 +431,7 @@ int build_index(const seismic_csr *docs, const seismic_build_params *bp, seismic
     ix->has_full = 1;
   }
 
+  timer.mark("full lists");
   // ---- pruned lists: top-lambda_t postings by (value desc, doc asc)
   std::vector<uint32_t> lptr(d + 1, 0);
   for (uint32_t t = 0; t < d; t++) {
@@ -426,6 +469,7 @@ int build_index(const seismic_csr *docs, const seismic_build_params *bp, seismic
   std::vector<uint32_t>().swap(fdoc);
   std::vector<float>().swap(fval);
 
+  timer.mark("pruned lists");
   // ---- centroids: partial Fisher-Yates per list, splitmix64(seed ^ t*golden)
   std::vector<uint32_t> cptr2(d + 1, 0);
   for (uint32_t t = 0; t < d; t++) {
@@ -451,6 +495,7 @@ int build_index(const seismic_csr *docs, const seismic_build_params *bp, seismic
     }
   });
 
+  timer.mark("centroids");
   // ---- clustering on the device
   std::vector<uint32_t> assign(npost);
   {
@@ -479,6 +524,7 @@ int build_index(const seismic_csr *docs, const seismic_build_params *bp, seismic
     if (npost) SZ_CUDA(cudaMemcpy(assign.data(), d_asg.p, npost * 4, cudaMemcpyDeviceToHost));
   }
 
+  timer.mark("clustering (device)");
   // ---- blocks (non-empty clusters in centroid order; members ascending)
   std::vector<uint32_t> nblk_of(d, 0);
   parallel_for(d, T, [&](int64_t t, int) {
@@ -524,6 +570,7 @@ int build_index(const seismic_csr *docs, const seismic_build_params *bp, seismic
   ix->max_blocks_per_list = maxnb;
   std::vector<uint32_t>().swap(cdoc);
 
+  timer.mark("blocks");
   // ---- summaries: max vector, alpha-MSS, quantisation (per list, block-major)
   struct ListSum {
     std::vector<uint32_t> cnt;  // kept entries per block
@@ -619,6 +666,7 @@ int build_index(const seismic_csr *docs, const seismic_build_params *bp, seismic
       }
     });
   }
+  timer.mark("summaries (max, alpha-MSS, u8)");
   std::vector<uint32_t> sptr(nblk + 1, 0);
   {
     uint64_t acc = 0;
@@ -652,8 +700,21 @@ int build_index(const seismic_csr *docs, const seismic_build_params *bp, seismic
     std::vector<uint16_t> cblk(nsum);
     std::vector<uint8_t> ccode(quant ? nsum : 0);
     std::vector<float> cval(quant ? 0 : nsum);
-    const uint64_t stride = (uint64_t)d + 1;
-    std::unique_ptr<uint32_t[]> dir(new uint32_t[(size_t)d * stride]);
+    // directory: presence bitmap of each list's summary terms, column base per
+    // 32-term word, and per-list column pointers (columns + 1 sentinel)
+    const uint32_t W = (d + 31) / 32;
+    std::vector<uint32_t> ncols(d, 0);
+    parallel_for(d, T, [&](int64_t t, int) {
+      std::vector<uint8_t> has(d, 0);
+      for (uint16_t s : ls[t].term) has[s] = 1;
+      uint32_t c = 0;
+      for (uint32_t s = 0; s < d; s++) c += has[s];
+      ncols[t] = c;
+    });
+    std::vector<uint64_t> cbase(d + 1, 0);
+    for (uint32_t t = 0; t < d; t++) cbase[t + 1] = cbase[t] + ncols[t] + 1;
+    if (cbase[d] > 0xFFFFFFFFull) return fail(SEISMIC_EINVAL, "more than 2^32 summary columns");
+    std::vector<uint32_t> sbmv((size_t)d * W * 2, 0u), cptrv(cbase[d]);
     parallel_for(d, T, [&](int64_t t, int) {
       const ListSum &L = ls[t];
       uint32_t g0 = bptr[t], nb = bptr[t + 1] - g0;
@@ -668,16 +729,19 @@ int build_index(const seismic_csr *docs, const seismic_build_params *bp, seismic
         if (quant) std::memcpy(&scode[base], L.code.data(), L.code.size());
       }
       // term-major layout of this list: columns by term, blocks ascending inside a column
-      uint32_t *dr = dir.get() + (size_t)t * stride;
-      std::fill(dr, dr + stride, 0u);
-      for (uint16_t s : L.term) dr[s + 1]++;
-      uint32_t run = base;
-      for (uint64_t s = 0; s <= d; s++) {
-        uint32_t c = (s < d) ? dr[s + 1] : 0;
-        dr[s] = run;
-        run += c;
+      std::vector<uint32_t> cnt(d, 0), cur(d, 0);
+      for (uint16_t s : L.term) cnt[s]++;
+      uint32_t run = base, col = (uint32_t)cbase[t];
+      uint32_t *bw = sbmv.data() + (size_t)t * W * 2;
+      for (uint32_t s = 0; s < d; s++) {
+        if ((s & 31) == 0) bw[2 * (s >> 5) + 1] = col;
+        if (!cnt[s]) continue;
+        bw[2 * (s >> 5)] |= 1u << (s & 31);
+        cptrv[col++] = run;
+        cur[s] = run;
+        run += cnt[s];
       }
-      std::vector<uint32_t> cur(dr, dr + d);
+      cptrv[col] = run;  // the list's sentinel
       uint32_t e = 0;
       for (uint32_t b = 0; b < nb; b++)
         for (uint32_t i = 0; i < L.cnt[b]; i++, e++) {
@@ -701,21 +765,18 @@ int build_index(const seismic_csr *docs, const seismic_build_params *bp, seismic
     } else if ((rc = upload(ix->scol_val, cval))) {
       return rc;
     }
-    if ((rc = ix->sdir.alloc((size_t)d * stride * 4))) return rc;
-    SZ_CUDA(cudaMemcpy(ix->sdir.p, dir.get(), (size_t)d * stride * 4, cudaMemcpyHostToDevice));
+    if ((rc = upload(ix->sbm, sbmv)) || (rc = upload(ix->scptr, cptrv))) return rc;
   }
   if ((rc = upload(ix->list_ptr, lptr)) || (rc = upload(ix->list_doc, ldoc)) || (rc = upload(ix->cent, assign)) ||
       (rc = upload(ix->blk_ptr, bptr)) || (rc = upload(ix->bdoc_ptr, bdptr)) || (rc = upload(ix->bdoc, bdoc)))
     return rc;
-  {  // each member's forward row (first chunk, chunk count) beside its id: one dependent load fewer
+  {  // each member's forward row (first unit, chunk count) beside its id: one dependent load fewer
     std::vector<uint64_t> brow(npost);
-    parallel_for((int64_t)npost, T, [&](int64_t p, int) {
-      const uint32_t j = bdoc[p];
-      brow[p] = (uint64_t)cptr[j] | ((uint64_t)(cptr[j + 1] - cptr[j]) << 32);
-    });
+    parallel_for((int64_t)npost, T, [&](int64_t p, int) { brow[p] = frow[bdoc[p]]; });
     if ((rc = upload(ix->bdoc_row, brow))) return rc;
   }
   SZ_CUDA(cudaDeviceSynchronize());
+  timer.mark("summary layout, uploads");
   *out = ix.release();
   return SEISMIC_OK;
 }

@@ -1,5 +1,7 @@
 // The C ABI (include/seismic.h): argument checks, staging of host buffers,
 // kernel dispatch, graph install, persistence and inspection.
+#include <cuda_fp16.h>
+
 #include <cstdio>
 #include <memory>
 #include <new>
@@ -33,25 +35,36 @@ __global__ void k_max_row_nnz(const uint64_t *indptr, uint64_t n, uint32_t *out)
 }
 
 // A flat CSR view of forward-index rows [r0, r0 + n): every padded row entry
-// is kept (the padding has value 0, which every reader ignores).
-__global__ void k_fwd_to_csr(const uint32_t *cptr, const uint8_t *data, uint64_t r0, uint64_t n, uint64_t *ip,
-                             uint16_t *terms, float *vals) {
-  const uint64_t base = 8ull * cptr[r0];
+// is kept (the padding has value 0, which every reader ignores).  ip[0..n]
+// (8 entries per chunk, prefix-summed) is given.
+__global__ void k_fwd_to_csr(const unsigned long long *frow, const uint8_t *data, int fp16, uint64_t r0, uint64_t n,
+                             const uint64_t *ip, uint16_t *terms, float *vals) {
   for (uint64_t i = blockIdx.x; i < n; i += gridDim.x) {
-    const uint32_t c0 = cptr[r0 + i], nch = cptr[r0 + i + 1] - c0;
-    const uint32_t P = nch * 8;
-    const uint16_t *tt = reinterpret_cast<const uint16_t *>(data + (size_t)c0 * 48);
-    const float *vv = reinterpret_cast<const float *>(data + (size_t)c0 * 48 + 2 * (size_t)P);
-    const uint64_t o = 8ull * c0 - base;
-    for (uint32_t j = threadIdx.x; j < P; j += blockDim.x) {
-      terms[o + j] = tt[j];
-      vals[o + j] = vv[j];
-    }
-    if (threadIdx.x == 0) {
-      ip[i] = o;
-      if (i == n - 1) ip[n] = 8ull * cptr[r0 + n] - base;
+    const unsigned long long row = frow[r0 + i];
+    const uint32_t nch = (uint32_t)(row >> 32);
+    const uint8_t *rec = data + (size_t)(uint32_t)row * kUnitBytes;
+    const uint64_t o = ip[i];
+    for (uint32_t j = threadIdx.x; j < 8 * nch; j += blockDim.x) {
+      const uint32_t c = j / 8, e = j % 8;
+      if (fp16) {
+        terms[o + j] = reinterpret_cast<const uint16_t *>(rec + (size_t)kUnitBytes * c)[e];
+        vals[o + j] = __half2float(reinterpret_cast<const __half *>(rec + (size_t)kUnitBytes * c + 16)[e]);
+      } else {
+        terms[o + j] = reinterpret_cast<const uint16_t *>(rec)[j];
+        vals[o + j] = reinterpret_cast<const float *>(rec + (size_t)kUnitBytes * ((nch + 1) / 2))[j];
+      }
     }
   }
+}
+
+// Bits per stored kappa-NN id: the smallest b with 2^b > n_docs, which is the
+// paper's floor(log2(n_docs - 1)) + 1 (Section 4.3) except when n_docs is a
+// power of two, where one more bit leaves the all-ones code free for a
+// missing neighbour.
+uint32_t knn_bits_for(uint64_t n) {
+  uint32_t b = 1;
+  while (b < 32 && (1ull << b) <= n) b++;
+  return b;
 }
 
 // Work-queue order of a persistent search: queries sorted by their largest
@@ -171,13 +184,16 @@ int check_params(const seismic_index *ix, const seismic_search_params *p) {
     return fail(SEISMIC_EINVAL, "cta_warps must be 1/2/4 (warp shape) or 4/8/16 (CTA shape)");
   uint32_t hs = p->hash_slots ? p->hash_slots : 2048;
   if (hs & (hs - 1)) return fail(SEISMIC_EINVAL, "hash_slots must be a power of two");
+  if (!(p->ctas_per_sm == 0 || p->ctas_per_sm == 5 || (p->ctas_per_sm == 6 && !ws && g == 1 && w == 8)))
+    return fail(SEISMIC_EINVAL, "ctas_per_sm must be 0, 5, or 6 (CTA shape, group 1, 8 warps)");
   return SEISMIC_OK;
 }
 
 }  // namespace
 
 int search_ws(seismic_index *ix, Workspace *w, const seismic_csr *queries, const seismic_search_params *p,
-              uint32_t *ids_out, float *scores_out, int32_t out_on_device, void *stream, uint64_t *stats) {
+              uint32_t *ids_out, float *scores_out, int32_t out_on_device, void *stream, uint64_t *stats,
+              const uint32_t *seed) {
   if (!ix || !queries || !w) return fail(SEISMIC_EINVAL, "NULL index/queries");
   int rc = check_params(ix, p);
   if (rc) return rc;
@@ -204,8 +220,9 @@ int search_ws(seismic_index *ix, Workspace *w, const seismic_csr *queries, const
     d_stats = w->stats.as<unsigned long long>();
   }
   SearchArgs a{};
-  a.fwd_cptr = ix->fwd_cptr.as<uint32_t>();
+  a.fwd_row = ix->fwd_row.as<unsigned long long>();
   a.fwd_data = ix->fwd_data.as<uint8_t>();
+  a.fp16 = ix->bp.values_fp16 ? 1 : 0;
   a.fwd_nnz = ix->fwd_nnz.as<uint16_t>();
   a.blk_ptr = ix->blk_ptr.as<uint32_t>();
   a.bdoc_ptr = ix->bdoc_ptr.as<uint32_t>();
@@ -213,12 +230,14 @@ int search_ws(seismic_index *ix, Workspace *w, const seismic_csr *queries, const
   a.bdoc_row = ix->bdoc_row.as<unsigned long long>();
   a.blk_m = ix->blk_m.as<float>();
   a.blk_size = ix->blk_size.as<float>();
-  a.sdir = ix->sdir.as<uint32_t>();
+  a.sbm = ix->sbm.as<uint2>();
+  a.scptr = ix->scptr.as<uint32_t>();
   a.scol_blk = ix->scol_blk.as<uint16_t>();
   a.scol_code = ix->scol_code.as<uint8_t>();
   a.scol_val = ix->scol_val.as<float>();
   a.knn = ix->knn.as<uint32_t>();
   a.kappa = ix->kappa;
+  a.knn_bits = ix->knn_bits;
   a.dim = ix->dim;
   a.quant = ix->bp.quantize_u8 ? 1 : 0;
   a.q_indptr = q.ip;
@@ -236,6 +255,9 @@ int search_ws(seismic_index *ix, Workspace *w, const seismic_csr *queries, const
   a.ids = d_ids;
   a.scores = d_sc;
   a.stats = d_stats;
+  a.seed = seed;
+  if (seed && (p->shape == 2 || !p->use_knn || p->k != ix->kappa + 1))
+    return fail(SEISMIC_EINVAL, "graph refinement runs the CTA shape with the expansion and k = kappa + 1");
   a.queue = w->queue.as<uint32_t>();
   a.persistent = p->persistent ? 1 : 0;
   a.W = (ix->dim + 31) / 32;
@@ -310,13 +332,13 @@ int search_ws(seismic_index *ix, Workspace *w, const seismic_csr *queries, const
     a.HS = 16;
     smem = search_layout(a, nw);
     int blocks = 1;
-    if ((rc = search_occupancy(group, nw, smem, &blocks))) return rc;
+    if ((rc = search_occupancy(group, nw, smem, &blocks, p->ctas_per_sm))) return rc;
     grid = (uint32_t)std::min<uint64_t>(nq, (uint64_t)std::max(1, blocks) * sm_count(ix->device));
     a.seen_words = (uint32_t)(((ix->n_docs + 31) / 32 + 3) & ~3ull);
     if ((rc = w->seen.ensure((size_t)grid * a.seen_words * 4))) return rc;
     a.seen_bm = w->seen.as<uint32_t>();
   }
-  if ((rc = launch_search(a, group, nw, smem, grid, st))) return rc;
+  if ((rc = launch_search(a, group, nw, smem, grid, st, p->ctas_per_sm))) return rc;
   }
   if (!out_on_device) {
     SZ_CUDA(cudaMemcpyAsync(ids_out, d_ids, (size_t)nq * k * 4, cudaMemcpyDeviceToHost, st));
@@ -402,10 +424,20 @@ int set_knn_impl(seismic_index *ix, const uint32_t *nbrs, uint64_t n, uint32_t k
   }
   for (uint64_t i = 0; i < n * kappa; i++)
     if (src[i] != SEISMIC_NONE_ID && src[i] >= n) return fail(SEISMIC_EINVAL, "knn: neighbour id out of range");
-  int rc = ix->knn.alloc(n * kappa * 4);
-  if (rc) return rc;
-  SZ_CUDA(cudaMemcpy(ix->knn.p, src, n * kappa * 4, cudaMemcpyHostToDevice));
+  // pack the ids back to back, `bits` each, low bits first
+  const uint32_t bits = knn_bits_for(n);
+  const uint64_t none = (1ull << bits) - 1ull, entries = n * kappa;
+  std::vector<uint32_t> words((entries * bits + 31) / 32 + 1, 0u);
+  for (uint64_t e = 0; e < entries; e++) {
+    const uint64_t v = src[e] == SEISMIC_NONE_ID ? none : (uint64_t)src[e];
+    const uint64_t b = e * bits;
+    const uint64_t w = b >> 5, sh = b & 31;
+    words[w] |= (uint32_t)(v << sh);
+    if (sh + bits > 32) words[w + 1] |= (uint32_t)(v >> (32 - sh));
+  }
+  if (int rc = upload(ix->knn, words)) return rc;
   ix->kappa = kappa;
+  ix->knn_bits = bits;
   return SEISMIC_OK;
 }
 
@@ -422,8 +454,8 @@ int build_knn_impl(seismic_index *ix, uint32_t kappa, const seismic_search_param
   const uint64_t batch = 1u << 16;
   std::vector<uint32_t> graph(N * kappa, SEISMIC_NONE_ID);
   DevBuf ip, tt, vv, ids, sc;
-  std::vector<uint32_t> cptr(N + 1);
-  SZ_CUDA(cudaMemcpy(cptr.data(), ix->fwd_cptr.p, (N + 1) * 4, cudaMemcpyDeviceToHost));
+  std::vector<uint64_t> frow(N), hip(batch + 1);
+  SZ_CUDA(cudaMemcpy(frow.data(), ix->fwd_row.p, N * 8, cudaMemcpyDeviceToHost));
   int rc;
   if ((rc = ids.alloc(batch * kk * 4)) || (rc = sc.alloc(batch * kk * 4)) || (rc = ip.alloc((batch + 1) * 8)))
     return rc;
@@ -438,13 +470,20 @@ int build_knn_impl(seismic_index *ix, uint32_t kappa, const seismic_search_param
   }
   for (uint64_t r0 = 0; r0 < N; r0 += batch) {
     const uint64_t n = std::min(batch, N - r0);
-    const uint64_t ent = 8ull * (cptr[r0 + n] - cptr[r0]);
-    if ((rc = tt.ensure(ent * 2 + 16)) || (rc = vv.ensure(ent * 4 + 16))) return rc;
-    k_fwd_to_csr<<<(unsigned)std::min<uint64_t>(n, 65535), 64>>>(ix->fwd_cptr.as<uint32_t>(), ix->fwd_data.as<uint8_t>(),
-                                                                 r0, n, ip.as<uint64_t>(), tt.as<uint16_t>(), vv.as<float>());
-    SZ_CUDA(cudaGetLastError());
     uint32_t mx = 0;
-    for (uint64_t i = r0; i < r0 + n; i++) mx = std::max(mx, 8u * (cptr[i + 1] - cptr[i]));
+    hip[0] = 0;
+    for (uint64_t i = 0; i < n; i++) {
+      const uint32_t e = 8u * (uint32_t)(frow[r0 + i] >> 32);
+      hip[i + 1] = hip[i] + e;
+      mx = std::max(mx, e);
+    }
+    const uint64_t ent = hip[n];
+    if ((rc = tt.ensure(ent * 2 + 16)) || (rc = vv.ensure(ent * 4 + 16))) return rc;
+    SZ_CUDA(cudaMemcpy(ip.p, hip.data(), (n + 1) * 8, cudaMemcpyHostToDevice));
+    k_fwd_to_csr<<<(unsigned)std::min<uint64_t>(n, 65535), 64>>>(ix->fwd_row.as<unsigned long long>(),
+                                                                 ix->fwd_data.as<uint8_t>(), ix->bp.values_fp16, r0, n,
+                                                                 ip.as<uint64_t>(), tt.as<uint16_t>(), vv.as<float>());
+    SZ_CUDA(cudaGetLastError());
     seismic_csr qc{ip.as<uint64_t>(), tt.as<uint16_t>(), vv.as<float>(), n, ix->dim, 1};
     if (p) {
       sp.max_query_nnz = mx;
@@ -466,24 +505,97 @@ int build_knn_impl(seismic_index *ix, uint32_t kappa, const seismic_search_param
   return set_knn_impl(ix, graph.data(), N, kappa, 0);
 }
 
+// Neighbour-of-neighbour passes over the installed graph (not a step of the
+// paper, whose Section 4.3 builds the graph approximately with the method
+// itself; this applies the method's expansion step to the graph): in each
+// round every document u is scored against its own list and its neighbours'
+// lists, and keeps the kappa best of them other than itself.  A round reads
+// only the graph from before it.
+int refine_knn_impl(seismic_index *ix, uint32_t rounds, const seismic_search_params *p) {
+  if (!ix) return fail(SEISMIC_EINVAL, "NULL index");
+  if (!ix->kappa) return fail(SEISMIC_EINVAL, "refine: the index has no kappa-NN graph");
+  if (ix->kappa + 1 > kMaxK) return fail(SEISMIC_EINVAL, "kappa too large");
+  SZ_CUDA(cudaSetDevice(ix->device));
+  const uint64_t N = ix->n_docs, batch = 1u << 16;
+  const uint32_t kappa = ix->kappa, kk = kappa + 1;
+  std::vector<uint64_t> frow(N), hip(batch + 1);
+  SZ_CUDA(cudaMemcpy(frow.data(), ix->fwd_row.p, N * 8, cudaMemcpyDeviceToHost));
+  DevBuf ip, tt, vv, ids, sc, seeds;
+  int rc;
+  if ((rc = ids.alloc(batch * kk * 4)) || (rc = sc.alloc(batch * kk * 4)) || (rc = ip.alloc((batch + 1) * 8)) ||
+      (rc = seeds.alloc(batch * 4)))
+    return rc;
+  std::vector<uint32_t> hid(batch * kk), hseed(batch);
+  seismic_search_params sp{};
+  if (p) sp = *p;
+  sp.k = kk;
+  sp.cut = 1;
+  sp.heap_factor = 1.0f;
+  sp.use_knn = 1;
+  sp.learned = 0;
+  sp.exhaustive = 0;
+  sp.alpha_q = 0.0f;
+  sp.shape = 1;
+  sp.persistent = 1;
+  for (uint32_t round = 0; round < rounds; round++) {
+    std::vector<uint32_t> graph(N * kappa, SEISMIC_NONE_ID);
+    for (uint64_t r0 = 0; r0 < N; r0 += batch) {
+      const uint64_t n = std::min(batch, N - r0);
+      uint32_t mx = 0;
+      hip[0] = 0;
+      for (uint64_t i = 0; i < n; i++) {
+        const uint32_t e = 8u * (uint32_t)(frow[r0 + i] >> 32);
+        hip[i + 1] = hip[i] + e;
+        mx = std::max(mx, e);
+        hseed[i] = (uint32_t)(r0 + i);
+      }
+      if ((rc = tt.ensure(hip[n] * 2 + 16)) || (rc = vv.ensure(hip[n] * 4 + 16))) return rc;
+      SZ_CUDA(cudaMemcpy(ip.p, hip.data(), (n + 1) * 8, cudaMemcpyHostToDevice));
+      SZ_CUDA(cudaMemcpy(seeds.p, hseed.data(), n * 4, cudaMemcpyHostToDevice));
+      k_fwd_to_csr<<<(unsigned)std::min<uint64_t>(n, 65535), 64>>>(ix->fwd_row.as<unsigned long long>(),
+                                                                   ix->fwd_data.as<uint8_t>(), ix->bp.values_fp16, r0,
+                                                                   n, ip.as<uint64_t>(), tt.as<uint16_t>(),
+                                                                   vv.as<float>());
+      SZ_CUDA(cudaGetLastError());
+      seismic_csr qc{ip.as<uint64_t>(), tt.as<uint16_t>(), vv.as<float>(), n, ix->dim, 1};
+      sp.max_query_nnz = mx;
+      if ((rc = search_ws(ix, &ix->ws, &qc, &sp, ids.as<uint32_t>(), sc.as<float>(), 1, nullptr, nullptr,
+                          seeds.as<uint32_t>())))
+        return rc;
+      SZ_CUDA(cudaMemcpy(hid.data(), ids.p, n * kk * 4, cudaMemcpyDeviceToHost));
+      for (uint64_t i = 0; i < n; i++) {
+        const uint32_t self = (uint32_t)(r0 + i);
+        uint32_t o = 0;
+        for (uint32_t j = 0; j < kk && o < kappa; j++) {
+          const uint32_t v = hid[i * kk + j];
+          if (v == self) continue;
+          graph[(r0 + i) * kappa + o++] = v;
+        }
+      }
+    }
+    if ((rc = set_knn_impl(ix, graph.data(), N, kappa, 0))) return rc;
+  }
+  return SEISMIC_OK;
+}
+
 // ---------------------------------------------------------------- persistence
 namespace {
 constexpr char kMagic[8] = {'S', 'E', 'I', 'S', 'M', 'I', 'C', '1'};
-constexpr uint32_t kVersion = 2;
+constexpr uint32_t kVersion = 3;
 
 struct FileHead {
   char magic[8];
   uint32_t version, dim;
   uint64_t n_docs, nnz, n_postings, n_blocks, n_sum;
-  uint32_t max_blocks_per_list, max_block_docs, kappa, has_full, has_mlp, quant;
+  uint32_t max_blocks_per_list, max_block_docs, kappa, has_full, has_mlp, quant, knn_bits;
   float sum_absmax;
   seismic_build_params bp;
 };
 
 DevBuf *file_bufs(seismic_index *ix, int i) {
-  DevBuf *b[] = {&ix->fwd_cptr, &ix->fwd_data, &ix->fwd_nnz, &ix->list_ptr, &ix->list_doc, &ix->cent, &ix->blk_ptr,
+  DevBuf *b[] = {&ix->fwd_row, &ix->fwd_data, &ix->fwd_nnz, &ix->list_ptr, &ix->list_doc, &ix->cent, &ix->blk_ptr,
                  &ix->bdoc_ptr, &ix->bdoc, &ix->bdoc_row, &ix->blk_m, &ix->blk_size, &ix->sum_ptr, &ix->sum_term, &ix->sum_val,
-                 &ix->sum_code, &ix->sdir, &ix->scol_blk, &ix->scol_code, &ix->scol_val, &ix->full_ptr,
+                 &ix->sum_code, &ix->sbm, &ix->scptr, &ix->scol_blk, &ix->scol_code, &ix->scol_val, &ix->full_ptr,
                  &ix->full_doc, &ix->full_val, &ix->knn, &ix->mlp};
   return i < (int)(sizeof(b) / sizeof(b[0])) ? b[i] : nullptr;
 }
@@ -507,6 +619,7 @@ int save_impl(const seismic_index *cix, const char *path) {
   h.max_blocks_per_list = ix->max_blocks_per_list;
   h.max_block_docs = ix->max_block_docs;
   h.kappa = ix->kappa;
+  h.knn_bits = ix->knn_bits;
   h.has_full = ix->has_full;
   h.has_mlp = ix->has_mlp;
   h.quant = ix->bp.quantize_u8;
@@ -545,6 +658,7 @@ int load_impl(const char *path, seismic_index **out) {
   ix->max_blocks_per_list = h.max_blocks_per_list;
   ix->max_block_docs = h.max_block_docs;
   ix->kappa = h.kappa;
+  ix->knn_bits = h.knn_bits;
   ix->has_full = h.has_full;
   ix->has_mlp = h.has_mlp;
   ix->bp = h.bp;
@@ -630,12 +744,25 @@ int seismic_build_knn(seismic_index *index, uint32_t kappa, const seismic_search
   SZ_GUARD(build_knn_impl(index, kappa, params));
 }
 
+int seismic_refine_knn(seismic_index *index, uint32_t rounds, const seismic_search_params *params) {
+  SZ_GUARD(refine_knn_impl(index, rounds, params));
+}
+
 int seismic_get_knn(const seismic_index *index, uint32_t *nbrs, uint64_t cap_entries) {
   if (!index || !nbrs) return fail(SEISMIC_EINVAL, "NULL argument");
   if (!index->kappa) return fail(SEISMIC_EINVAL, "the index has no kappa-NN graph");
-  uint64_t n = index->n_docs * index->kappa;
+  const uint64_t n = index->n_docs * index->kappa, bits = index->knn_bits, none = (1ull << bits) - 1ull;
   if (cap_entries < n) return fail(SEISMIC_EINVAL, "buffer too small");
-  SZ_CUDA(cudaMemcpy(nbrs, index->knn.p, n * 4, cudaMemcpyDeviceToHost));
+  std::vector<uint32_t> words(index->knn.bytes / 4);
+  SZ_CUDA(cudaSetDevice(index->device));
+  SZ_CUDA(cudaMemcpy(words.data(), index->knn.p, words.size() * 4, cudaMemcpyDeviceToHost));
+  for (uint64_t e = 0; e < n; e++) {
+    const uint64_t b = e * bits, w = b >> 5, sh = b & 31;
+    uint64_t x = words[w];
+    if (sh + bits > 32) x |= (uint64_t)words[w + 1] << 32;
+    const uint64_t v = (x >> sh) & none;
+    nbrs[e] = v == none ? SEISMIC_NONE_ID : (uint32_t)v;
+  }
   return SEISMIC_OK;
 }
 
@@ -656,6 +783,9 @@ int seismic_info(const seismic_index *ix, seismic_index_info *out) {
   out->has_full_lists = ix->has_full;
   out->has_mlp = ix->has_mlp;
   out->device_bytes = device_bytes(ix);
+  out->values_fp16 = ix->bp.values_fp16;
+  out->knn_bits = ix->knn_bits;
+  out->knn_bytes = ix->kappa ? ix->knn.bytes : 0;
   return SEISMIC_OK;
 }
 

@@ -80,8 +80,9 @@ extern "C" int seismic_search_noalloc(seismic_index *ix, const seismic_csr *quer
   SZ_CUDA(cudaMemsetAsync(queue, 0, 16, st));
 
   SearchArgs a{};
-  a.fwd_cptr = ix->fwd_cptr.as<uint32_t>();
+  a.fwd_row = ix->fwd_row.as<unsigned long long>();
   a.fwd_data = ix->fwd_data.as<uint8_t>();
+  a.fp16 = ix->bp.values_fp16 ? 1 : 0;
   a.fwd_nnz = ix->fwd_nnz.as<uint16_t>();
   a.blk_ptr = ix->blk_ptr.as<uint32_t>();
   a.bdoc_ptr = ix->bdoc_ptr.as<uint32_t>();
@@ -89,12 +90,14 @@ extern "C" int seismic_search_noalloc(seismic_index *ix, const seismic_csr *quer
   a.bdoc_row = ix->bdoc_row.as<unsigned long long>();
   a.blk_m = ix->blk_m.as<float>();
   a.blk_size = ix->blk_size.as<float>();
-  a.sdir = ix->sdir.as<uint32_t>();
+  a.sbm = ix->sbm.as<uint2>();
+  a.scptr = ix->scptr.as<uint32_t>();
   a.scol_blk = ix->scol_blk.as<uint16_t>();
   a.scol_code = ix->scol_code.as<uint8_t>();
   a.scol_val = ix->scol_val.as<float>();
   a.knn = ix->knn.as<uint32_t>();
   a.kappa = ix->kappa;
+  a.knn_bits = ix->knn_bits;
   a.dim = ix->dim;
   a.quant = ix->bp.quantize_u8 ? 1 : 0;
   a.q_indptr = queries->indptr;
@@ -128,12 +131,12 @@ extern "C" int seismic_search_noalloc(seismic_index *ix, const seismic_csr *quer
   const size_t smem = search_layout(a, nw);
   if (smem > 200 * 1024) return fail(SEISMIC_EBUDGET, "search: shared memory per query exceeds 200 KB");
   int blocks = 1;
-  if ((rc = search_occupancy(group, nw, smem, &blocks))) return rc;
+  if ((rc = search_occupancy(group, nw, smem, &blocks, p->ctas_per_sm))) return rc;
   int sms = 1;
   SZ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device));
   uint64_t grid = std::min<uint64_t>(nq, (uint64_t)std::max(1, blocks) * sms);
   grid = std::min<uint64_t>(grid, cap_ctas);
   a.seen_words = (uint32_t)words;
   a.seen_bm = reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(scratch) + kNoAllocHeader);
-  return launch_search(a, group, nw, smem, (uint32_t)grid, st);
+  return launch_search(a, group, nw, smem, (uint32_t)grid, st, p->ctas_per_sm);
 }

@@ -226,7 +226,7 @@ __device__ void eval_wave(const SearchArgs &a, Smem &s, Shared &sh, uint32_t n, 
       uint32_t d;
       unsigned long long row;
       src.fetch(i, d, row);
-      if (d != SEISMIC_NONE_ID) prefetch_row(a.fwd_data, row);
+      if (d != SEISMIC_NONE_ID) prefetch_row(a.fwd_data, row, a.fp16);
     }
   }
   // Software pipeline per lane group: the next document's (id, row) are loaded
@@ -246,8 +246,7 @@ __device__ void eval_wave(const SearchArgs &a, Smem &s, Shared &sh, uint32_t n, 
       if (s.seen) old = atomicOr(s.seen + (d >> 5), bit);
       else fresh = seen_insert(s.hash(), a.HS - 1u, d, &sh.hash_full) ? 1u : 0u;
     }
-    const float p = row_dot<G>(a.fwd_data, (uint32_t)row, (uint32_t)(row >> 32), gl, gmask, s.qbits(), s.qrank(),
-                               s.qval());
+    const float p = row_dot<G>(a.fwd_data, row, a.fp16, gl, gmask, s.qbits(), s.qrank(), s.qval());
     if (s.seen) fresh = (old & bit) ? 0u : 1u;
     fresh = __shfl_sync(gmask, fresh, 0, G);
     if (!fresh) continue;
@@ -318,9 +317,10 @@ __device__ uint32_t block_exclusive_scan(uint32_t *v, uint32_t n, uint32_t *wtmp
 // terms added in entry order; a document's score is the sum of its chunks'
 // partials in chunk order (deterministic, independent of the launch shape).
 // Work per thread is balanced whatever the row lengths; seen documents cost
-// no row reads, and a row's values are read only where its term is in the
-// query (a 4-byte read-only load each; most entries miss).
-template <int NT, class Src>
+// no row reads.  fp32 rows: a chunk's values (one 32-byte sector) are read
+// only where a term is in the query (4-byte read-only loads; most chunks of a
+// row miss).  fp16 rows: a chunk is one sector, terms and values read together.
+template <int NT, bool FP16, class Src>
 __device__ __forceinline__ void eval_wave_flat(const SearchArgs &a, Smem &s, Shared &sh, uint32_t n, const Src &src,
                                                int knn_stage) {
   constexpr int U = 2;
@@ -345,7 +345,7 @@ __device__ __forceinline__ void eval_wave_flat(const SearchArgs &a, Smem &s, Sha
       if (fresh) {
         keep = d;
         nch = (uint32_t)(row >> 32);
-        if (a.prefetch) prefetch_row(a.fwd_data, row);
+        if (a.prefetch) prefetch_row(a.fwd_data, row, a.fp16);
         if (a.stats) {
           atomicAdd(&sh.st[knn_stage ? SEISMIC_ST_KNN_DOCS : SEISMIC_ST_DOCS], 1ull);
           atomicAdd(&sh.st[knn_stage ? SEISMIC_ST_KNN_NNZ : SEISMIC_ST_DOC_NNZ], (unsigned long long)a.fwd_nnz[d]);
@@ -383,7 +383,7 @@ __device__ __forceinline__ void eval_wave_flat(const SearchArgs &a, Smem &s, Sha
     for (uint32_t j = tid; j < total; j += NT * U) {
       // a row holds its chunks' terms (16 B each), then their values (32 B each):
       // the terms are read first and a value only where the term is in the query
-      uint4 t[U];
+      uint4 t[U], vh[U];
       const float *vp[U];
 #pragma unroll
       for (int u = 0; u < U; u++) {  // past the end: the last chunk again (unconditional loads stay in registers)
@@ -391,9 +391,10 @@ __device__ __forceinline__ void eval_wave_flat(const SearchArgs &a, Smem &s, Sha
         {
           const uint32_t i = s.cmap()[jj], p0 = s.fpre()[i];
           const uint32_t nch = s.fpre()[i + 1] - p0, o = base + jj - p0;
-          const uint8_t *row = a.fwd_data + (size_t)s.fc0()[i] * 48;
-          t[u] = ldg_na(row + 16 * o);
-          vp[u] = reinterpret_cast<const float *>(row + 16 * nch + 32 * o);
+          const uint8_t *rec = a.fwd_data + (size_t)s.fc0()[i] * kUnitBytes;
+          t[u] = ldg_na(chunk_terms(rec, o, FP16));
+          vp[u] = reinterpret_cast<const float *>(chunk_vals(rec, nch, o, FP16));
+          if (FP16) vh[u] = ldg_na(vp[u]);
         }
       }
 #pragma unroll
@@ -401,12 +402,18 @@ __device__ __forceinline__ void eval_wave_flat(const SearchArgs &a, Smem &s, Sha
         const uint32_t jj = j + u * NT;
         if (jj < total) {
           const uint32_t tw[4] = {t[u].x, t[u].y, t[u].z, t[u].w};
+          const uint32_t hw[4] = {vh[u].x, vh[u].y, vh[u].z, vh[u].w};
           float acc = 0.0f;
 #pragma unroll
           for (int e = 0; e < 8; e++) {  // absent terms (most) cost one shared load and no value read
             const uint32_t tt = (e & 1) ? (tw[e >> 1] >> 16) : (tw[e >> 1] & 0xFFFFu);
             const uint32_t w = qb[tt >> 5], sh5 = tt & 31u;
-            if ((w >> sh5) & 1u) acc = fmaf(qv[qr[tt >> 5] + __popc(w & ((1u << sh5) - 1u))], __ldg(vp[u] + e), acc);
+            if ((w >> sh5) & 1u) {
+              float v;
+              if (FP16) v = __half2float(__ushort_as_half((unsigned short)((e & 1) ? (hw[e >> 1] >> 16) : (hw[e >> 1] & 0xFFFFu))));
+              else v = __ldg(vp[u] + e);
+              acc = fmaf(qv[qr[tt >> 5] + __popc(w & ((1u << sh5) - 1u))], v, acc);
+            }
           }
           cpart[jj] = acc;
         }
@@ -434,8 +441,12 @@ __device__ __forceinline__ void eval_wave_flat(const SearchArgs &a, Smem &s, Sha
 template <int G, int NT, class Src>
 __device__ __forceinline__ void eval(const SearchArgs &a, Smem &s, Shared &sh, uint32_t n, const Src &src,
                                      int knn_stage) {
-  if constexpr (G == 1) eval_wave_flat<NT>(a, s, sh, n, src, knn_stage);
-  else eval_wave<G, NT>(a, s, sh, n, src, knn_stage);
+  if constexpr (G == 1) {
+    if (a.fp16) eval_wave_flat<NT, true>(a, s, sh, n, src, knn_stage);
+    else eval_wave_flat<NT, false>(a, s, sh, n, src, knn_stage);
+  } else {
+    eval_wave<G, NT>(a, s, sh, n, src, knn_stage);
+  }
 }
 
 template <int NT>
@@ -455,9 +466,10 @@ __device__ void bitonic_sort_u64(unsigned long long *keys, uint32_t P2) {
     }
 }
 
-// 5 CTAs of 256 threads per SM (48 registers)
-template <int G, int NW>
-__global__ void __launch_bounds__(NW * 32, 1280 / (NW * 32))
+// MB CTAs per SM: 5 of 256 threads by default (48 registers), 6 for the
+// 40-register build of the chunk-flattened 8-warp kernel
+template <int G, int NW, int MB>
+__global__ void __launch_bounds__(NW * 32, MB)
     k_search(const __grid_constant__ SearchArgs a) {
   constexpr int NT = NW * 32;
   __shared__ Shared sh;
@@ -488,7 +500,7 @@ __global__ void __launch_bounds__(NW * 32, 1280 / (NW * 32))
     } else {
       for (uint32_t i = tid; i < a.HS; i += NT) s.hash()[i] = 0u;
     }
-    if (tid < SEISMIC_STATS_N) sh.st[tid] = 0ull;
+    if (tid < SEISMIC_STATS_N) sh.st[tid] = tid == SEISMIC_ST_T_START && a.stats ? globaltimer_ns() : 0ull;
     if (tid == 0) {
       sh.count = 0; sh.ncand = 0; sh.nvalid = 0; sh.hash_full = 0; sh.bad = 0;
       sh.cut = a.cut;
@@ -572,7 +584,7 @@ __global__ void __launch_bounds__(NW * 32, 1280 / (NW * 32))
       if (tid == 0) sh.ncut = min(cut, nzq);
     }
     __syncthreads();
-    const uint32_t ncut = sh.ncut;
+    const uint32_t ncut = a.seed ? 0u : sh.ncut;  // graph refinement: no lists
     const float hf = sh.hf;
     if (a.stats && tid == 0) sh.st[SEISMIC_ST_QUERY_NNZ] = nnz;
 
@@ -596,11 +608,11 @@ __global__ void __launch_bounds__(NW * 32, 1280 / (NW * 32))
         continue;
       }
       // ---- H2: summary scores of every block of the list
-      const size_t dbase = (size_t)t * (a.dim + 1u);
-      for (uint32_t i = tid; i < nzq; i += NT) {
-        const uint32_t sterm = s.qterm()[i];
-        s.clo()[i] = __ldg(a.sdir + dbase + sterm);
-        s.chi()[i] = __ldg(a.sdir + dbase + sterm + 1);
+      {
+        uint32_t words = 0;
+        for (uint32_t i = tid; i < nzq; i += NT)
+          words += summary_column(a.sbm, a.scptr, a.W, t, s.qterm()[i], s.clo() + i, s.chi() + i);
+        if (a.stats && words) atomicAdd(&sh.st[SEISMIC_ST_DIR_LOOKUPS], (unsigned long long)words);
       }
       for (uint32_t i = tid; i < NW * a.BMAX; i += NT) s.part()[i] = 0.0f;
       for (uint32_t b = tid; b <= nb; b += NT) s.bptr()[b] = __ldg(a.bdoc_ptr + g0 + b);  // block member ranges
@@ -637,10 +649,7 @@ __global__ void __launch_bounds__(NW * 32, 1280 / (NW * 32))
           s.keys()[b] = ~0ull;
         }
       }
-      if (a.stats && tid == 0) {
-        sh.st[SEISMIC_ST_BLOCKS_SCORED] += nb;
-        sh.st[SEISMIC_ST_DIR_LOOKUPS] += 2ull * nzq;
-      }
+      if (a.stats && tid == 0) sh.st[SEISMIC_ST_BLOCKS_SCORED] += nb;
       __syncthreads();
       // ---- H3: order blocks by (r desc, block asc)
       bitonic_sort_u64<NT>(s.keys(), P2);
@@ -693,6 +702,12 @@ __global__ void __launch_bounds__(NW * 32, 1280 / (NW * 32))
       __syncthreads();
     }
 
+    // graph refinement: the heap starts from the document and its neighbours
+    if (a.seed) {
+      const SeedSrc src{a.seed[q], a.knn, a.fwd_row, a.kappa, a.knn_bits};
+      eval<G, NT>(a, s, sh, 1 + a.kappa, src, 0);
+    }
+
     // ---------------------------------------------------------- H7: kappa-NN expansion
     if (a.use_knn && a.kappa > 0 && sh.count > 0) {
       const uint32_t ns = sh.count;
@@ -701,7 +716,7 @@ __global__ void __launch_bounds__(NW * 32, 1280 / (NW * 32))
       const uint32_t total = ns * a.kappa;
       for (uint32_t c0 = 0; c0 < total; c0 += a.CAND) {
         const uint32_t n = min(a.CAND, total - c0);
-        const GraphSrc src{s.clo(), a.knn + (size_t)0, a.fwd_cptr, a.kappa};
+        const GraphSrc src{s.clo(), a.knn, a.fwd_row, a.kappa, a.knn_bits};
         // positions c0 .. c0 + n of the neighbour list of S
         struct Shifted {
           GraphSrc g;
@@ -720,26 +735,27 @@ __global__ void __launch_bounds__(NW * 32, 1280 / (NW * 32))
       a.ids[(size_t)q * a.k + i] = ok ? s.tk_id()[i] : SEISMIC_NONE_ID;
       a.scores[(size_t)q * a.k + i] = ok ? s.tk_s()[i] : -INFINITY;
     }
+    if (a.stats && tid == SEISMIC_ST_T_END) sh.st[tid] = globaltimer_ns();
     if (a.stats && tid < SEISMIC_STATS_N) a.stats[(size_t)q * SEISMIC_STATS_N + tid] = sh.st[tid];
     __syncthreads();
     if (!a.persistent) break;
   }
 }
 
-template <int G, int NW>
+template <int G, int NW, int MB>
 int launch_t(const SearchArgs &a, size_t smem, uint32_t grid, cudaStream_t st) {
   static std::atomic<uint64_t> configured{0};
-  int rc = set_smem_limit_once(configured, (const void *)k_search<G, NW>, 200 * 1024);
+  int rc = set_smem_limit_once(configured, (const void *)k_search<G, NW, MB>, 200 * 1024);
   if (rc) return rc;
-  k_search<G, NW><<<grid, NW * 32, smem, st>>>(a);
+  k_search<G, NW, MB><<<grid, NW * 32, smem, st>>>(a);
   SZ_CUDA(cudaGetLastError());
   return SEISMIC_OK;
 }
 
-template <int G, int NW>
+template <int G, int NW, int MB>
 int occupancy_t(size_t smem, int *blocks) {
-  SZ_CUDA(cudaFuncSetAttribute(k_search<G, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  SZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_search<G, NW>, NW * 32, smem));
+  SZ_CUDA(cudaFuncSetAttribute(k_search<G, NW, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  SZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_search<G, NW, MB>, NW * 32, smem));
   return SEISMIC_OK;
 }
 
@@ -790,9 +806,14 @@ size_t search_layout(SearchArgs &a, uint32_t nw) {
   return o;
 }
 
-int launch_search(const SearchArgs &a, uint32_t group, uint32_t nw, size_t smem, uint32_t grid, cudaStream_t st) {
+int launch_search(const SearchArgs &a, uint32_t group, uint32_t nw, size_t smem, uint32_t grid, cudaStream_t st,
+                  uint32_t ctas_per_sm) {
+  if (ctas_per_sm == 6) {
+    if (group == 1 && nw == 8) return launch_t<1, 8, 6>(a, smem, grid, st);
+    return fail(SEISMIC_EINVAL, "ctas_per_sm = 6 needs group 1 and 8 warps");
+  }
 #define SZ_CASE(G_, NW_) \
-  if (group == G_ && nw == NW_) return launch_t<G_, NW_>(a, smem, grid, st);
+  if (group == G_ && nw == NW_) return launch_t<G_, NW_, 1280 / (NW_ * 32)>(a, smem, grid, st);
   SZ_CASE(1, 4) SZ_CASE(1, 8) SZ_CASE(1, 16)
   SZ_CASE(8, 4) SZ_CASE(8, 8) SZ_CASE(8, 16)
   SZ_CASE(16, 4) SZ_CASE(16, 8) SZ_CASE(16, 16)
@@ -801,9 +822,13 @@ int launch_search(const SearchArgs &a, uint32_t group, uint32_t nw, size_t smem,
   return fail(SEISMIC_EINVAL, "group must be 1/8/16/32 and cta_warps 4/8/16");
 }
 
-int search_occupancy(uint32_t group, uint32_t nw, size_t smem, int *blocks) {
+int search_occupancy(uint32_t group, uint32_t nw, size_t smem, int *blocks, uint32_t ctas_per_sm) {
+  if (ctas_per_sm == 6) {
+    if (group == 1 && nw == 8) return occupancy_t<1, 8, 6>(smem, blocks);
+    return fail(SEISMIC_EINVAL, "ctas_per_sm = 6 needs group 1 and 8 warps");
+  }
 #define SZ_CASE(G_, NW_) \
-  if (group == G_ && nw == NW_) return occupancy_t<G_, NW_>(smem, blocks);
+  if (group == G_ && nw == NW_) return occupancy_t<G_, NW_, 1280 / (NW_ * 32)>(smem, blocks);
   SZ_CASE(1, 4) SZ_CASE(1, 8) SZ_CASE(1, 16)
   SZ_CASE(8, 4) SZ_CASE(8, 8) SZ_CASE(8, 16)
   SZ_CASE(16, 4) SZ_CASE(16, 8) SZ_CASE(16, 16)

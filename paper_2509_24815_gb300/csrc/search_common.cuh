@@ -1,10 +1,18 @@
 // Device helpers shared by the two search kernels (CTA per query, warp per query).
 #pragma once
 
+#include <cuda_fp16.h>
+
 #include "search_impl.h"
 
 namespace seismic {
 namespace dev {
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 // float <-> order-preserving u32
 __device__ __forceinline__ uint32_t f2ord(float f) {
@@ -49,18 +57,46 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
   if (n) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"(n) : "memory");
 }
 
-// <q, row> for a forward-index row of nch 8-entry chunks starting at chunk c0
-// (16 B of terms, then 32 B of values per chunk).  G lanes cooperate: lane gl
-// takes chunks gl, gl + G, ... and keeps U of them in flight; it adds its
-// products in chunk order and the G partial sums are combined by a fixed
+// Forward rows (see the layout in seismic_impl.h): a row descriptor is its
+// first 32-byte unit | its chunk count << 32.
+__device__ __forceinline__ const uint8_t *row_base(const uint8_t *fwd, unsigned long long row) {
+  return fwd + (size_t)(uint32_t)row * kUnitBytes;
+}
+// chunk o's 16 bytes of terms, and the address of its values
+__device__ __forceinline__ const uint8_t *chunk_terms(const uint8_t *rec, uint32_t o, int fp16) {
+  return rec + (fp16 ? kUnitBytes : 16u) * (size_t)o;
+}
+__device__ __forceinline__ const uint8_t *chunk_vals(const uint8_t *rec, uint32_t nch, uint32_t o, int fp16) {
+  return fp16 ? rec + (size_t)kUnitBytes * o + 16 : rec + (size_t)kUnitBytes * ((nch + 1) / 2 + o);
+}
+
+// Adds q[t_e] * v_e over one chunk's 8 entries to acc (in entry order):
+// tw = the chunk's terms, v = its values as 8 fp32 or 8 fp16 in 4 words.
+__device__ __forceinline__ float chunk_dot(const uint32_t tw[4], const uint32_t vv[8], int fp16,
+                                           const uint32_t *__restrict__ qbits, const uint16_t *__restrict__ qrank,
+                                           const float *__restrict__ qval, float acc) {
+#pragma unroll
+  for (int e = 0; e < 8; e++) {
+    const uint32_t t = (e & 1) ? (tw[e >> 1] >> 16) : (tw[e >> 1] & 0xFFFFu);
+    float v;
+    if (fp16) v = __half2float(__ushort_as_half((unsigned short)((e & 1) ? (vv[e >> 1] >> 16) : (vv[e >> 1] & 0xFFFFu))));
+    else v = __uint_as_float(vv[e]);
+    acc = fmaf(qlookup(qbits, qrank, qval, t), v, acc);
+  }
+  return acc;
+}
+
+// <q, row> for a forward-index row of nch 8-entry chunks.  G lanes cooperate:
+// lane gl takes chunks gl, gl + G, ... and keeps U of them in flight; it adds
+// its products in chunk order and the G partial sums are combined by a fixed
 // butterfly, so the result depends on G only.
 template <int G>
-__device__ __forceinline__ float row_dot(const uint8_t *__restrict__ fwd, uint32_t c0, uint32_t nch, int gl,
+__device__ __forceinline__ float row_dot(const uint8_t *__restrict__ fwd, unsigned long long row, int fp16, int gl,
                                          uint32_t gmask, const uint32_t *__restrict__ qbits,
                                          const uint16_t *__restrict__ qrank, const float *__restrict__ qval) {
   constexpr int U = G >= 16 ? 2 : 16 / G;
-  const uint8_t *rec = fwd + (size_t)c0 * 48;
-  const uint8_t *vrec = rec + 16 * (size_t)nch;
+  const uint8_t *rec = row_base(fwd, row);
+  const uint32_t nch = (uint32_t)(row >> 32);
   float acc = 0.0f;
 #pragma unroll 1
   for (uint32_t c = gl; c < nch; c += U * G) {
@@ -68,14 +104,14 @@ __device__ __forceinline__ float row_dot(const uint8_t *__restrict__ fwd, uint32
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const uint32_t cc = c + u * G;
+      t[u] = make_uint4(0u, 0u, 0u, 0u);
+      va[u] = t[u];
+      vb[u] = t[u];
       if (cc < nch) {
-        t[u] = ldg_na(rec + 16 * (size_t)cc);
-        va[u] = ldg_na(vrec + 32 * (size_t)cc);
-        vb[u] = ldg_na(vrec + 32 * (size_t)cc + 16);
-      } else {
-        t[u] = make_uint4(0u, 0u, 0u, 0u);
-        va[u] = t[u];
-        vb[u] = t[u];
+        t[u] = ldg_na(chunk_terms(rec, cc, fp16));
+        const uint8_t *vp = chunk_vals(rec, nch, cc, fp16);
+        va[u] = ldg_na(vp);
+        if (!fp16) vb[u] = ldg_na(vp + 16);
       }
     }
 #pragma unroll
@@ -83,11 +119,7 @@ __device__ __forceinline__ float row_dot(const uint8_t *__restrict__ fwd, uint32
       if (c + u * G >= nch) break;
       const uint32_t tw[4] = {t[u].x, t[u].y, t[u].z, t[u].w};
       const uint32_t vv[8] = {va[u].x, va[u].y, va[u].z, va[u].w, vb[u].x, vb[u].y, vb[u].z, vb[u].w};
-#pragma unroll
-      for (int e = 0; e < 4; e++) {
-        acc = fmaf(qlookup(qbits, qrank, qval, tw[e] & 0xFFFFu), __uint_as_float(vv[2 * e]), acc);
-        acc = fmaf(qlookup(qbits, qrank, qval, tw[e] >> 16), __uint_as_float(vv[2 * e + 1]), acc);
-      }
+      acc = chunk_dot(tw, vv, fp16, qbits, qrank, qval, acc);
     }
   }
 #pragma unroll
@@ -95,8 +127,36 @@ __device__ __forceinline__ float row_dot(const uint8_t *__restrict__ fwd, uint32
   return acc;
 }
 
-__device__ __forceinline__ void prefetch_row(const uint8_t *fwd, unsigned long long row) {
-  prefetch_l2(fwd + (size_t)(uint32_t)row * 48, 48u * (uint32_t)(row >> 32));
+__device__ __forceinline__ void prefetch_row(const uint8_t *fwd, unsigned long long row, int fp16) {
+  prefetch_l2(row_base(fwd, row), kUnitBytes * row_units((uint32_t)(row >> 32), fp16));
+}
+
+// The summary column of term s in list t: [*lo, *hi) in the scol_* arrays
+// (empty when the list's summaries never hold s).  Returns the 4-byte words
+// read (2 for the presence word, 2 more for a column's bounds).
+__device__ __forceinline__ uint32_t summary_column(const uint2 *__restrict__ sbm, const uint32_t *__restrict__ scptr,
+                                                   uint32_t W, uint32_t t, uint32_t s, uint32_t *lo, uint32_t *hi) {
+  const uint2 e = __ldg(sbm + (size_t)t * W + (s >> 5));
+  const uint32_t bit = 1u << (s & 31);
+  if (!(e.x & bit)) {
+    *lo = 0;
+    *hi = 0;
+    return 2;
+  }
+  const uint32_t c = e.y + __popc(e.x & (bit - 1u));
+  *lo = __ldg(scptr + c);
+  *hi = __ldg(scptr + c + 1);
+  return 4;
+}
+
+// Entry e of the bit-packed kappa-NN graph (bits per id; all ones = missing).
+__device__ __forceinline__ uint32_t knn_entry(const uint32_t *__restrict__ words, uint32_t bits, uint64_t e) {
+  const uint64_t b = e * bits;
+  const uint32_t w = (uint32_t)(b >> 5), sh = (uint32_t)(b & 31);
+  uint64_t x = __ldg(words + w);
+  if (sh + bits > 32) x |= (uint64_t)__ldg(words + w + 1) << 32;
+  const uint32_t v = (uint32_t)(x >> sh) & (uint32_t)((1ull << bits) - 1ull);
+  return v == (uint32_t)((1ull << bits) - 1ull) ? SEISMIC_NONE_ID : v;
 }
 
 // Document sources: id(i), and row(i, id) = first chunk | chunks << 32.
@@ -113,19 +173,35 @@ struct MemberSrc {  // a contiguous range of block members (ids and rows side by
 };
 
 struct GraphSrc {  // the kappa-NN neighbours of the ids in S
-  const uint32_t *S, *knn, *cptr;
-  uint32_t kappa;
+  const uint32_t *S, *knn;
+  const unsigned long long *frow;
+  uint32_t kappa, bits;
   __device__ __forceinline__ uint32_t id(uint32_t x) const {
-    return __ldg(knn + (size_t)S[x / kappa] * kappa + (x % kappa));
+    return knn_entry(knn, bits, (uint64_t)S[x / kappa] * kappa + (x % kappa));
   }
   __device__ __forceinline__ unsigned long long row(uint32_t, uint32_t d) const {
-    if (d == SEISMIC_NONE_ID) return 0ull;
-    const uint32_t c0 = __ldg(cptr + d);
-    return (unsigned long long)c0 | ((unsigned long long)(__ldg(cptr + d + 1) - c0) << 32);
+    return d == SEISMIC_NONE_ID ? 0ull : __ldg(frow + d);
   }
   __device__ __forceinline__ void fetch(uint32_t x, uint32_t &d, unsigned long long &r) const {
     d = id(x);
     r = row(x, d);
+  }
+};
+
+struct SeedSrc {  // a document, then its kappa-NN neighbours
+  uint32_t doc;
+  const uint32_t *knn;
+  const unsigned long long *frow;
+  uint32_t kappa, bits;
+  __device__ __forceinline__ uint32_t id(uint32_t i) const {
+    return i == 0 ? doc : knn_entry(knn, bits, (uint64_t)doc * kappa + (i - 1));
+  }
+  __device__ __forceinline__ unsigned long long row(uint32_t, uint32_t d) const {
+    return d == SEISMIC_NONE_ID ? 0ull : __ldg(frow + d);
+  }
+  __device__ __forceinline__ void fetch(uint32_t i, uint32_t &d, unsigned long long &r) const {
+    d = id(i);
+    r = row(i, d);
   }
 };
 

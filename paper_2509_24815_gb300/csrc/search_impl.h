@@ -7,8 +7,9 @@ namespace seismic {
 
 struct SearchArgs {
   // index
-  const uint32_t *fwd_cptr;
+  const unsigned long long *fwd_row;  // per document: first 32-byte unit | chunks << 32
   const uint8_t *fwd_data;
+  int fp16;                           // forward values are fp16 (unit per chunk) rather than fp32
   const uint16_t *fwd_nnz;
   const uint32_t *blk_ptr;
   const uint32_t *bdoc_ptr;
@@ -16,12 +17,13 @@ struct SearchArgs {
   const unsigned long long *bdoc_row;  // member's forward row: first chunk | chunks << 32
   const float *blk_m;
   const float *blk_size;
-  const uint32_t *sdir;
+  const uint2 *sbm;       // summary directory: presence bits + column base per 32-term word of a list
+  const uint32_t *scptr;  // column pointers into scol_*
   const uint16_t *scol_blk;
   const uint8_t *scol_code;
   const float *scol_val;
-  const uint32_t *knn;
-  uint32_t kappa;
+  const uint32_t *knn;    // bit-packed ids, knn_bits each
+  uint32_t kappa, knn_bits;
   uint32_t dim;
   int quant;
   // queries: CSR rows
@@ -53,6 +55,10 @@ struct SearchArgs {
   float sum_absmax;
   uint32_t prefetch;  // rows of the next block prefetched into L2 (at most this many; 0 = off)
   const uint32_t *perm;  // persistent launches pull queries in this order (NULL: 0, 1, 2, ...)
+  // graph refinement (CTA kernel): query q is document seed[q]; its lists are
+  // not traversed, the heap is seeded with the document and its graph row, and
+  // the kappa-NN expansion follows (NULL: ordinary search)
+  const uint32_t *seed;
   // CTA kernel, group 1: documents are scored chunk by chunk by all threads
   // of the CTA (a wave's chunks laid end to end, then summed per document)
   uint32_t flat;
@@ -65,11 +71,18 @@ struct SearchArgs {
 
 constexpr uint32_t kMaxWave = 64;  // blocks per wave (CTA kernel)
 size_t search_layout(SearchArgs &a, uint32_t nw);
-int launch_search(const SearchArgs &a, uint32_t group, uint32_t nw, size_t smem, uint32_t grid, cudaStream_t st);
-int search_occupancy(uint32_t group, uint32_t nw, size_t smem, int *blocks);
+// ctas_per_sm: 0 or 5 = the default build, 6 = the 40-register build (group 1, 8 warps only)
+int launch_search(const SearchArgs &a, uint32_t group, uint32_t nw, size_t smem, uint32_t grid, cudaStream_t st,
+                  uint32_t ctas_per_sm = 0);
+int search_occupancy(uint32_t group, uint32_t nw, size_t smem, int *blocks, uint32_t ctas_per_sm = 0);
 size_t search_layout_warp(SearchArgs &a);
 int launch_search_warp(const SearchArgs &a, uint32_t group, size_t smem, uint32_t grid, uint32_t wpb,
                        cudaStream_t st);
+// One search call on a workspace (the C ABI's seismic_search, the server's
+// streams); `seed` selects the graph-refinement mode above.
+int search_ws(seismic_index *ix, Workspace *w, const seismic_csr *queries, const seismic_search_params *p,
+              uint32_t *ids_out, float *scores_out, int32_t out_on_device, void *stream, uint64_t *stats,
+              const uint32_t *seed = nullptr);
 int search_occupancy_warp(uint32_t group, uint32_t k, size_t smem, uint32_t wpb, int *blocks);
 
 struct ExactArgs {

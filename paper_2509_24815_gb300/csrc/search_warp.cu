@@ -141,7 +141,7 @@ __device__ void eval_docs(const SearchArgs &a, const WarpSmem &s, uint32_t *seen
     }
     float p = -INFINITY;
     if (d != SEISMIC_NONE_ID)
-      p = row_dot<G>(a.fwd_data, (uint32_t)row, (uint32_t)(row >> 32), gl, gmask, s.qbits, s.qrank, s.qval);
+      p = row_dot<G>(a.fwd_data, row, a.fp16, gl, gmask, s.qbits, s.qrank, s.qval);
     uint32_t fresh = (d != SEISMIC_NONE_ID && !(old & bit)) ? 1u : 0u;
     fresh = __shfl_sync(0xffffffffu, fresh, grp * G);
     if (fresh && a.stats && gl == 0) {
@@ -200,6 +200,7 @@ __global__ void __launch_bounds__(128, 5) k_search_warp(const SearchArgs a) {
     WarpCounters st;
     if (a.stats)
       for (int i = 0; i < SEISMIC_STATS_N; i++) st.v[i] = 0ull;
+      if (a.stats && lane == 0) st.v[SEISMIC_ST_T_START] = globaltimer_ns();  // lanes' partials are summed
 
     // ---------------------------------------------------------- H0
     const uint64_t qb = a.q_indptr[q], qe = a.q_indptr[q + 1];
@@ -325,15 +326,14 @@ __global__ void __launch_bounds__(128, 5) k_search_warp(const SearchArgs a) {
           continue;
         }
         // ---- H2: column ranges, flat offsets, fixed-point scores
-        const size_t dbase = (size_t)t * (a.dim + 1u);
-        uint32_t carry = 0;
+        uint32_t carry = 0, dir_words = 0;
         for (uint32_t i0 = 0; i0 < nzq; i0 += 32) {
           const uint32_t i = i0 + lane;
           uint32_t lo = 0, len = 0;
           if (i < nzq) {
-            const uint32_t sterm = s.qterm[i];
-            lo = __ldg(a.sdir + dbase + sterm);
-            len = __ldg(a.sdir + dbase + sterm + 1) - lo;
+            uint32_t hi;
+            dir_words += summary_column(a.sbm, a.scptr, a.W, t, s.qterm[i], &lo, &hi);
+            len = hi - lo;
             s.clo[i] = lo;
           }
           uint32_t tot;
@@ -342,6 +342,7 @@ __global__ void __launch_bounds__(128, 5) k_search_warp(const SearchArgs a) {
           carry += tot;
         }
         const uint32_t T = carry;
+        dir_words = __reduce_add_sync(0xffffffffu, dir_words);
         if (lane == 0) s.cofs[nzq] = T;
         for (uint32_t b = lane; b < nb; b += 32) s.rk[b] = 0ull;
         __syncwarp();
@@ -374,7 +375,7 @@ __global__ void __launch_bounds__(128, 5) k_search_warp(const SearchArgs a) {
         __syncwarp();
         if (a.stats && lane == 0) {
           st.v[SEISMIC_ST_BLOCKS_SCORED] += nb;
-          st.v[SEISMIC_ST_DIR_LOOKUPS] += 2ull * nzq;
+          st.v[SEISMIC_ST_DIR_LOOKUPS] += dir_words;
           st.v[SEISMIC_ST_SUMMARY_ENTRIES] += T;
         }
         // ---- H3: warp bitonic sort
@@ -407,7 +408,7 @@ __global__ void __launch_bounds__(128, 5) k_search_warp(const SearchArgs a) {
           const uint32_t e0 = __ldg(a.bdoc_ptr + g0 + bb), e1 = min(__ldg(a.bdoc_ptr + g0 + bb + 1), e0 + pf);
           for (uint32_t e = e0 + lane; e < e1; e += 32) {
             const unsigned long long row = __ldg(a.bdoc_row + e);
-            prefetch_l2(a.fwd_data + (size_t)(uint32_t)row * 48, 48u * (uint32_t)(row >> 32));
+            prefetch_row(a.fwd_data, row, a.fp16);
           }
         };
         members_l2(0);
@@ -446,7 +447,7 @@ __global__ void __launch_bounds__(128, 5) k_search_warp(const SearchArgs a) {
           if (e < ns) S[e] = tk.id[r];
         }
         __syncwarp();
-        const GraphSrc src{S, a.knn, a.fwd_cptr, a.kappa};
+        const GraphSrc src{S, a.knn, a.fwd_row, a.kappa, a.knn_bits};
         eval_docs<G, R>(a, s, seen, tk, ns * a.kappa, src, lane, st, 1);
       }
       // ------------------------------------------------------ output
@@ -460,6 +461,7 @@ __global__ void __launch_bounds__(128, 5) k_search_warp(const SearchArgs a) {
         }
       }
       if (a.stats) {
+        if (lane == 0) st.v[SEISMIC_ST_T_END] = globaltimer_ns();
         for (int i = 0; i < SEISMIC_STATS_N; i++) {
           unsigned long long v = st.v[i];
 #pragma unroll

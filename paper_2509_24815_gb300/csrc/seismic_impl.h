@@ -102,11 +102,19 @@ template <class T> int upload(DevBuf &b, const std::vector<T> &v) {
   return SEISMIC_OK;
 }
 
-// Forward-index layout: each row is padded to a multiple of 8 entries and
-// stored as one 48-byte-aligned record: P u16 terms, then P fp32 values
-// (P = 8 * chunks).  Padding entries are (term 0, value 0), which add 0.
+// Forward-index layout.  Each row is padded to a multiple of 8 entries (c
+// chunks; padding entries are (term 0, value 0), which add 0) and stored as a
+// record that starts on a 32-byte DRAM sector and fills whole sectors
+// ("units").  A row is addressed by its first unit and its chunk count.
+//   fp32 values: the 8c u16 terms (16c bytes, padded to a multiple of 32),
+//     then the 8c fp32 values, chunk o's 8 values in the 32-byte unit
+//     ceil(c/2) + o, so the values of one chunk are one sector;
+//     units per row = ceil(c/2) + c.
+//   fp16 values: chunk o is unit o, its 8 u16 terms then its 8 fp16 values;
+//     units per row = c.
 constexpr uint32_t kChunk = 8;
-constexpr uint32_t kChunkBytes = 48;
+constexpr uint32_t kUnitBytes = 32;
+__host__ __device__ inline uint32_t row_units(uint32_t nch, int fp16) { return fp16 ? nch : (nch + 1) / 2 + nch; }
 
 // Limits checked on the host before any device work.
 constexpr uint32_t kMaxRowNnzBuild = 8192;  // clustering stages a centroid chunk in shared memory
@@ -135,8 +143,8 @@ struct seismic_index {
   float sum_absmax = 0.0f;  // >= every |summary value| as the search dequantises it
 
   // forward index
-  seismic::DevBuf fwd_cptr;  // u32[n_docs+1] row start in 8-entry chunks
-  seismic::DevBuf fwd_data;  // 48 bytes per chunk
+  seismic::DevBuf fwd_row;   // u64[n_docs]: first 32-byte unit | chunks << 32
+  seismic::DevBuf fwd_data;  // the row records
   seismic::DevBuf fwd_nnz;   // u16[n_docs] true nonzeros per row (work counters only)
 
   // pruned lists, blocks
@@ -146,7 +154,7 @@ struct seismic_index {
   seismic::DevBuf blk_ptr;   // u32[dim+1]
   seismic::DevBuf bdoc_ptr;  // u32[n_blocks+1]
   seismic::DevBuf bdoc;      // u32[n_postings]
-  seismic::DevBuf bdoc_row;  // u64[n_postings]: member's forward row, first chunk | chunks << 32
+  seismic::DevBuf bdoc_row;  // u64[n_postings]: member's forward row, first unit | chunks << 32
   seismic::DevBuf blk_m;     // f32[n_blocks]
   seismic::DevBuf blk_size;  // f32[n_blocks]
 
@@ -157,7 +165,13 @@ struct seismic_index {
   seismic::DevBuf sum_code;  // u8[n_sum]
 
   // summaries, term-major per list (search)
-  seismic::DevBuf sdir;      // u32[dim * (dim+1)]: column s of list t = [sdir[t*(dim+1)+s], +1)
+  // summary directory: list t's column of term s exists iff bit s & 31 of
+  // sbm[t * W + s / 32].x is set (W = ceil(dim / 32)); its index is
+  // sbm[...].y + popcount of the lower bits of that word, and its entries are
+  // scol_*[scptr[index] .. scptr[index + 1]).  Each list's column pointers end
+  // with a sentinel, so memory is dim * W * 8 bytes + 4 per column.
+  seismic::DevBuf sbm;       // uint2[dim * W]: presence bits, first column index of the word
+  seismic::DevBuf scptr;     // u32[columns + dim]
   seismic::DevBuf scol_blk;  // u16[n_sum] local block index
   seismic::DevBuf scol_code; // u8[n_sum]
   seismic::DevBuf scol_val;  // f32[n_sum] (fp32 summaries)
@@ -168,9 +182,12 @@ struct seismic_index {
   seismic::DevBuf full_doc;  // u32[nnz]
   seismic::DevBuf full_val;  // f32[nnz]
 
-  // kappa-NN graph
+  // kappa-NN graph, ids bit-packed: entry e (= doc * kappa + slot) holds
+  // knn_bits bits starting at bit e * knn_bits of the u32 word array (low bits
+  // first); the all-ones code is a missing neighbour
   uint32_t kappa = 0;
-  seismic::DevBuf knn;       // u32[n_docs*kappa]
+  uint32_t knn_bits = 0;
+  seismic::DevBuf knn;
 
   // MLP
   int has_mlp = 0;

@@ -18,11 +18,6 @@
 
 #include "search_impl.h"
 
-namespace seismic {
-int search_ws(seismic_index *ix, Workspace *w, const seismic_csr *queries, const seismic_search_params *p,
-              uint32_t *ids_out, float *scores_out, int32_t out_on_device, void *stream, uint64_t *stats);
-size_t search_layout(SearchArgs &a, uint32_t nw);
-}  // namespace seismic
 
 using namespace seismic;
 using Clock = std::chrono::steady_clock;
@@ -249,7 +244,7 @@ int seismic_server_create(seismic_index *ix, const seismic_search_params *search
       a.flat = g == 1 ? 1u : 0u;
       size_t smem = search_layout(a, nw);
       int blocks = 1;
-      int rc = search_occupancy(g, nw, smem, &blocks);
+      int rc = search_occupancy(g, nw, smem, &blocks, search->ctas_per_sm);
       if (rc) return rc;
       int sms = 1;
       SZ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device));

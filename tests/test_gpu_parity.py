@@ -226,6 +226,42 @@ def test_approximate_knn_graph_build(sz, small, small_built):
 
 
 # ------------------------------------------------------------------ exact search
+def check_graph_rows(docs, g, ref, tol=TOL):
+    """Graph rows equal up to near-ties: where an entry differs, the fp64
+    scores of the two ids at that rank agree within 2 tol."""
+    assert g.shape == ref.shape
+    mism = g != ref
+    if not mism.any():
+        return 0
+    rows, cols = np.nonzero(mism)
+    a = oracle.pair_dots(docs, docs, rows.astype(np.uint64), g[rows, cols])
+    b = oracle.pair_dots(docs, docs, rows.astype(np.uint64), ref[rows, cols])
+    assert np.all(np.abs(a - b) <= 2 * tol * np.maximum(np.abs(b), 1e-30)), "graph rows differ beyond near-ties"
+    return int(mism.sum())
+
+
+def test_knn_refine_parity(sz, small, small_built):
+    """seismic_refine_knn against the oracle's neighbour-of-neighbour pass on
+    the same input graph, for two rounds; the graph moves towards the exact one."""
+    ix, _ = small_built[True]
+    docs = small["docs"]
+    sz.seismic_build_knn(ix, 6, sz.search_params(k=7, cut=2, heap_factor=1.0))  # a coarse first graph
+    g = sz.seismic_get_knn(ix)
+    exact = oracle.knn_exact(docs, 6)
+    frac = [(g == exact).mean()]
+    for _ in range(2):
+        ref = oracle.knn_refine(docs, g)
+        sz.seismic_refine_knn(ix, 1)
+        g = sz.seismic_get_knn(ix)
+        check_graph_rows(docs, g, ref)
+        frac.append((g == exact).mean())
+    assert frac[1] > frac[0] and frac[2] >= frac[1], frac
+    # the exact graph is a fixed point
+    sz.seismic_set_knn(ix, exact)
+    sz.seismic_refine_knn(ix, 1)
+    check_graph_rows(docs, sz.seismic_get_knn(ix), exact)
+
+
 def test_exact_search_matches_oracle(sz, small, small_built):
     ix, _ = small_built[True]
     docs, queries = small["docs"], small["queries"]
