@@ -122,9 +122,6 @@ typedef struct {
   uint32_t order;        /* persistent launches: 0 (default) runs queries grouped by their
                             largest term, so queries reading the same lists share L2; 1 runs
                             them in input order.  Results do not depend on it */
-  uint32_t ctas_per_sm;  /* CTA shape: 0 or 5 = the default build of the kernel (48 registers, 5
-                            CTAs of 8 warps per SM); 6 = a build capped at 40 registers so that 6
-                            share an SM (group 1 and 8 warps only).  A speed knob: same results */
 } seismic_search_params;
 
 /* Per-query work counters written by seismic_search when `stats` is non-NULL:

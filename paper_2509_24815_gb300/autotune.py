@@ -22,9 +22,10 @@ from . import DeviceCSR, search_params, seismic_info, seismic_search
 # (group 1: chunk-flattened scoring, else lane groups of that width), 2 = one
 # warp per query
 DEFAULT_CANDIDATES = tuple(
-    [(1, 1, w, v, pf) for w in (8, 16) for v in (4, 16, 32) for pf in (False, True)] +
+    [(1, 1, 8, v, pf) for v in (4, 8, 16, 32) for pf in (False, True)] +
+    [(1, 1, 16, v, pf) for v in (8, 16) for pf in (False, True)] +
     [(1, 8, 8, v, pf) for v in (4, 16) for pf in (False, True)] +
-    [(1, 16, 8, 16, True), (1, 8, 4, 16, True), (1, 8, 16, 16, True)] +
+    [(1, 16, 8, 16, True), (1, 8, 4, 16, True)] +
     [(2, g, 4, 1, pf) for g in (4, 8) for pf in (False, True)])
 
 

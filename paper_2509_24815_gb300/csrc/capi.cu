@@ -184,8 +184,6 @@ int check_params(const seismic_index *ix, const seismic_search_params *p) {
     return fail(SEISMIC_EINVAL, "cta_warps must be 1/2/4 (warp shape) or 4/8/16 (CTA shape)");
   uint32_t hs = p->hash_slots ? p->hash_slots : 2048;
   if (hs & (hs - 1)) return fail(SEISMIC_EINVAL, "hash_slots must be a power of two");
-  if (!(p->ctas_per_sm == 0 || p->ctas_per_sm == 5 || (p->ctas_per_sm == 6 && !ws && g == 1 && w == 8)))
-    return fail(SEISMIC_EINVAL, "ctas_per_sm must be 0, 5, or 6 (CTA shape, group 1, 8 warps)");
   return SEISMIC_OK;
 }
 
@@ -332,13 +330,13 @@ int search_ws(seismic_index *ix, Workspace *w, const seismic_csr *queries, const
     a.HS = 16;
     smem = search_layout(a, nw);
     int blocks = 1;
-    if ((rc = search_occupancy(group, nw, smem, &blocks, p->ctas_per_sm))) return rc;
+    if ((rc = search_occupancy(group, nw, smem, &blocks))) return rc;
     grid = (uint32_t)std::min<uint64_t>(nq, (uint64_t)std::max(1, blocks) * sm_count(ix->device));
     a.seen_words = (uint32_t)(((ix->n_docs + 31) / 32 + 3) & ~3ull);
     if ((rc = w->seen.ensure((size_t)grid * a.seen_words * 4))) return rc;
     a.seen_bm = w->seen.as<uint32_t>();
   }
-  if ((rc = launch_search(a, group, nw, smem, grid, st, p->ctas_per_sm))) return rc;
+  if ((rc = launch_search(a, group, nw, smem, grid, st))) return rc;
   }
   if (!out_on_device) {
     SZ_CUDA(cudaMemcpyAsync(ids_out, d_ids, (size_t)nq * k * 4, cudaMemcpyDeviceToHost, st));

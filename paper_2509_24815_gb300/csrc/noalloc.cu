@@ -131,12 +131,12 @@ extern "C" int seismic_search_noalloc(seismic_index *ix, const seismic_csr *quer
   const size_t smem = search_layout(a, nw);
   if (smem > 200 * 1024) return fail(SEISMIC_EBUDGET, "search: shared memory per query exceeds 200 KB");
   int blocks = 1;
-  if ((rc = search_occupancy(group, nw, smem, &blocks, p->ctas_per_sm))) return rc;
+  if ((rc = search_occupancy(group, nw, smem, &blocks))) return rc;
   int sms = 1;
   SZ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device));
   uint64_t grid = std::min<uint64_t>(nq, (uint64_t)std::max(1, blocks) * sms);
   grid = std::min<uint64_t>(grid, cap_ctas);
   a.seen_words = (uint32_t)words;
   a.seen_bm = reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(scratch) + kNoAllocHeader);
-  return launch_search(a, group, nw, smem, (uint32_t)grid, st, p->ctas_per_sm);
+  return launch_search(a, group, nw, smem, (uint32_t)grid, st);
 }

@@ -466,10 +466,10 @@ __device__ void bitonic_sort_u64(unsigned long long *keys, uint32_t P2) {
     }
 }
 
-// MB CTAs per SM: 5 of 256 threads by default (48 registers), 6 for the
-// 40-register build of the chunk-flattened 8-warp kernel
-template <int G, int NW, int MB>
-__global__ void __launch_bounds__(NW * 32, MB)
+// 5 CTAs of 256 threads per SM (48 registers).  A 40-register build for 6
+// CTAs per SM spilled little but measured 3-7 % slower at waves >= 4.
+template <int G, int NW>
+__global__ void __launch_bounds__(NW * 32, 1280 / (NW * 32))
     k_search(const __grid_constant__ SearchArgs a) {
   constexpr int NT = NW * 32;
   __shared__ Shared sh;
@@ -742,20 +742,20 @@ __global__ void __launch_bounds__(NW * 32, MB)
   }
 }
 
-template <int G, int NW, int MB>
+template <int G, int NW>
 int launch_t(const SearchArgs &a, size_t smem, uint32_t grid, cudaStream_t st) {
   static std::atomic<uint64_t> configured{0};
-  int rc = set_smem_limit_once(configured, (const void *)k_search<G, NW, MB>, 200 * 1024);
+  int rc = set_smem_limit_once(configured, (const void *)k_search<G, NW>, 200 * 1024);
   if (rc) return rc;
-  k_search<G, NW, MB><<<grid, NW * 32, smem, st>>>(a);
+  k_search<G, NW><<<grid, NW * 32, smem, st>>>(a);
   SZ_CUDA(cudaGetLastError());
   return SEISMIC_OK;
 }
 
-template <int G, int NW, int MB>
+template <int G, int NW>
 int occupancy_t(size_t smem, int *blocks) {
-  SZ_CUDA(cudaFuncSetAttribute(k_search<G, NW, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  SZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_search<G, NW, MB>, NW * 32, smem));
+  SZ_CUDA(cudaFuncSetAttribute(k_search<G, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  SZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_search<G, NW>, NW * 32, smem));
   return SEISMIC_OK;
 }
 
@@ -806,14 +806,9 @@ size_t search_layout(SearchArgs &a, uint32_t nw) {
   return o;
 }
 
-int launch_search(const SearchArgs &a, uint32_t group, uint32_t nw, size_t smem, uint32_t grid, cudaStream_t st,
-                  uint32_t ctas_per_sm) {
-  if (ctas_per_sm == 6) {
-    if (group == 1 && nw == 8) return launch_t<1, 8, 6>(a, smem, grid, st);
-    return fail(SEISMIC_EINVAL, "ctas_per_sm = 6 needs group 1 and 8 warps");
-  }
+int launch_search(const SearchArgs &a, uint32_t group, uint32_t nw, size_t smem, uint32_t grid, cudaStream_t st) {
 #define SZ_CASE(G_, NW_) \
-  if (group == G_ && nw == NW_) return launch_t<G_, NW_, 1280 / (NW_ * 32)>(a, smem, grid, st);
+  if (group == G_ && nw == NW_) return launch_t<G_, NW_>(a, smem, grid, st);
   SZ_CASE(1, 4) SZ_CASE(1, 8) SZ_CASE(1, 16)
   SZ_CASE(8, 4) SZ_CASE(8, 8) SZ_CASE(8, 16)
   SZ_CASE(16, 4) SZ_CASE(16, 8) SZ_CASE(16, 16)
@@ -822,13 +817,9 @@ int launch_search(const SearchArgs &a, uint32_t group, uint32_t nw, size_t smem,
   return fail(SEISMIC_EINVAL, "group must be 1/8/16/32 and cta_warps 4/8/16");
 }
 
-int search_occupancy(uint32_t group, uint32_t nw, size_t smem, int *blocks, uint32_t ctas_per_sm) {
-  if (ctas_per_sm == 6) {
-    if (group == 1 && nw == 8) return occupancy_t<1, 8, 6>(smem, blocks);
-    return fail(SEISMIC_EINVAL, "ctas_per_sm = 6 needs group 1 and 8 warps");
-  }
+int search_occupancy(uint32_t group, uint32_t nw, size_t smem, int *blocks) {
 #define SZ_CASE(G_, NW_) \
-  if (group == G_ && nw == NW_) return occupancy_t<G_, NW_, 1280 / (NW_ * 32)>(smem, blocks);
+  if (group == G_ && nw == NW_) return occupancy_t<G_, NW_>(smem, blocks);
   SZ_CASE(1, 4) SZ_CASE(1, 8) SZ_CASE(1, 16)
   SZ_CASE(8, 4) SZ_CASE(8, 8) SZ_CASE(8, 16)
   SZ_CASE(16, 4) SZ_CASE(16, 8) SZ_CASE(16, 16)

@@ -71,10 +71,8 @@ struct SearchArgs {
 
 constexpr uint32_t kMaxWave = 64;  // blocks per wave (CTA kernel)
 size_t search_layout(SearchArgs &a, uint32_t nw);
-// ctas_per_sm: 0 or 5 = the default build, 6 = the 40-register build (group 1, 8 warps only)
-int launch_search(const SearchArgs &a, uint32_t group, uint32_t nw, size_t smem, uint32_t grid, cudaStream_t st,
-                  uint32_t ctas_per_sm = 0);
-int search_occupancy(uint32_t group, uint32_t nw, size_t smem, int *blocks, uint32_t ctas_per_sm = 0);
+int launch_search(const SearchArgs &a, uint32_t group, uint32_t nw, size_t smem, uint32_t grid, cudaStream_t st);
+int search_occupancy(uint32_t group, uint32_t nw, size_t smem, int *blocks);
 size_t search_layout_warp(SearchArgs &a);
 int launch_search_warp(const SearchArgs &a, uint32_t group, size_t smem, uint32_t grid, uint32_t wpb,
                        cudaStream_t st);

@@ -244,7 +244,7 @@ int seismic_server_create(seismic_index *ix, const seismic_search_params *search
       a.flat = g == 1 ? 1u : 0u;
       size_t smem = search_layout(a, nw);
       int blocks = 1;
-      int rc = search_occupancy(g, nw, smem, &blocks, search->ctas_per_sm);
+      int rc = search_occupancy(g, nw, smem, &blocks);
       if (rc) return rc;
       int sms = 1;
       SZ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device));

@@ -147,7 +147,7 @@ def predict(weights: np.ndarray, features: np.ndarray):
 
 
 def calibrate(index, weights: np.ndarray, queries: DeviceCSR, gt_scores, k: int, target: float,
-              quantized: bool, base_params=None, margin: float = 0.005, max_shift: float = 6.0, iters: int = 10):
+              quantized: bool, base_params=None, margin: float = 0.005, max_shift: float = 12.0, iters: int = 12):
     """Shifts the cut output's bias (logit units) so that the learned form's
     mean recall on held-out training queries reaches `target + margin`: the
     smallest such shift in [0, max_shift] (the least work), found by bisection
@@ -183,10 +183,11 @@ def calibrate(index, weights: np.ndarray, queries: DeviceCSR, gt_scores, k: int,
 
 def fit(index, train_queries: DeviceCSR, host_train_queries, k: int = 10, target: float = 0.9,
         quantized: bool = True, steps: int = 3000, lr: float = 2e-3, seed: int = 0, base_params=None,
-        val_frac: float = 0.2):
+        val_frac: float = 0.2, grid_cut=GRID_CUT, grid_hf=GRID_HF, max_shift: float = 12.0):
     """Labels (trade-off form), features, training on the first part of the
     training queries, calibration on the rest; installs the network."""
-    cut0, hf0, table = label_queries(index, train_queries, k, target, quantized, base_params=base_params)
+    cut0, hf0, table = label_queries(index, train_queries, k, target, quantized, grid_cut=grid_cut, grid_hf=grid_hf,
+                                     base_params=base_params)
     cut, hf, lab_rec, lab_bytes = lagrangian_labels(table, target)
     feats = seismic_query_features(index, host_train_queries)
     n = host_train_queries.n_rows
@@ -195,7 +196,8 @@ def fit(index, train_queries: DeviceCSR, host_train_queries, k: int = 10, target
     val_host = host_train_queries.slice(ntr, n)
     val = DeviceCSR.from_host(val_host)
     _, gt_val = seismic_search_exact(index, val, k)
-    w, shift, val_rec = calibrate(index, w, val, gt_val.cpu().numpy(), k, target, quantized, base_params)
+    w, shift, val_rec = calibrate(index, w, val, gt_val.cpu().numpy(), k, target, quantized, base_params,
+                                  max_shift=max_shift)
     seismic_set_mlp(index, w)
     return dict(weights=w, trace=trace, label_cut=cut, label_hf=hf, label_recall=lab_rec, label_bytes=lab_bytes,
                 table=table, features=feats, calib_shift=shift, val_recall=val_rec)
