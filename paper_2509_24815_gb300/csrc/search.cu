@@ -320,7 +320,7 @@ __device__ uint32_t block_exclusive_scan(uint32_t *v, uint32_t n, uint32_t *wtmp
 // no row reads.  fp32 rows: a chunk's values (one 32-byte sector) are read
 // only where a term is in the query (4-byte read-only loads; most chunks of a
 // row miss).  fp16 rows: a chunk is one sector, terms and values read together.
-template <int NT, bool FP16, class Src>
+template <int NT, bool FP16, bool VSEC, class Src>
 __device__ __forceinline__ void eval_wave_flat(const SearchArgs &a, Smem &s, Shared &sh, uint32_t n, const Src &src,
                                                int knn_stage) {
   constexpr int U = 2;
@@ -383,7 +383,7 @@ __device__ __forceinline__ void eval_wave_flat(const SearchArgs &a, Smem &s, Sha
     for (uint32_t j = tid; j < total; j += NT * U) {
       // a row holds its chunks' terms (16 B each), then their values (32 B each):
       // the terms are read first and a value only where the term is in the query
-      uint4 t[U], vh[U];
+      uint4 t[U], vh[U], vl[U];
       const float *vp[U];
 #pragma unroll
       for (int u = 0; u < U; u++) {  // past the end: the last chunk again (unconditional loads stay in registers)
@@ -392,9 +392,13 @@ __device__ __forceinline__ void eval_wave_flat(const SearchArgs &a, Smem &s, Sha
           const uint32_t i = s.cmap()[jj], p0 = s.fpre()[i];
           const uint32_t nch = s.fpre()[i + 1] - p0, o = base + jj - p0;
           const uint8_t *rec = a.fwd_data + (size_t)s.fc0()[i] * kUnitBytes;
-          t[u] = ldg_na(chunk_terms(rec, o, FP16));
           vp[u] = reinterpret_cast<const float *>(chunk_vals(rec, nch, o, FP16));
-          if (FP16) vh[u] = ldg_na(vp[u]);
+          if (FP16) {
+            ldg_na_v8(chunk_terms(rec, o, true), t[u], vh[u]);  // the chunk's sector: terms, then halves
+          } else {
+            t[u] = ldg_na(chunk_terms(rec, o, false));
+            if (VSEC) ldg_na_v8(vp[u], vh[u], vl[u]);
+          }
         }
       }
 #pragma unroll
@@ -402,7 +406,7 @@ __device__ __forceinline__ void eval_wave_flat(const SearchArgs &a, Smem &s, Sha
         const uint32_t jj = j + u * NT;
         if (jj < total) {
           const uint32_t tw[4] = {t[u].x, t[u].y, t[u].z, t[u].w};
-          const uint32_t hw[4] = {vh[u].x, vh[u].y, vh[u].z, vh[u].w};
+          const uint32_t hw[8] = {vh[u].x, vh[u].y, vh[u].z, vh[u].w, vl[u].x, vl[u].y, vl[u].z, vl[u].w};
           float acc = 0.0f;
 #pragma unroll
           for (int e = 0; e < 8; e++) {  // absent terms (most) cost one shared load and no value read
@@ -411,6 +415,7 @@ __device__ __forceinline__ void eval_wave_flat(const SearchArgs &a, Smem &s, Sha
             if ((w >> sh5) & 1u) {
               float v;
               if (FP16) v = __half2float(__ushort_as_half((unsigned short)((e & 1) ? (hw[e >> 1] >> 16) : (hw[e >> 1] & 0xFFFFu))));
+              else if (VSEC) v = __uint_as_float(hw[e]);
               else v = __ldg(vp[u] + e);
               acc = fmaf(qv[qr[tt >> 5] + __popc(w & ((1u << sh5) - 1u))], v, acc);
             }
@@ -442,8 +447,9 @@ template <int G, int NT, class Src>
 __device__ __forceinline__ void eval(const SearchArgs &a, Smem &s, Shared &sh, uint32_t n, const Src &src,
                                      int knn_stage) {
   if constexpr (G == 1) {
-    if (a.fp16) eval_wave_flat<NT, true>(a, s, sh, n, src, knn_stage);
-    else eval_wave_flat<NT, false>(a, s, sh, n, src, knn_stage);
+    if (a.fp16) eval_wave_flat<NT, true, false>(a, s, sh, n, src, knn_stage);
+    else if (a.vsector) eval_wave_flat<NT, false, true>(a, s, sh, n, src, knn_stage);
+    else eval_wave_flat<NT, false, false>(a, s, sh, n, src, knn_stage);
   } else {
     eval_wave<G, NT>(a, s, sh, n, src, knn_stage);
   }

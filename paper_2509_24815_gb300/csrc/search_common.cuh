@@ -48,6 +48,14 @@ __device__ __forceinline__ uint4 ldg_na(const void *p) {
   return r;
 }
 
+// 32-byte read-only load (one DRAM sector) that does not allocate in L1; p is
+// 32-byte aligned
+__device__ __forceinline__ void ldg_na_v8(const void *p, uint4 &lo, uint4 &hi) {
+  asm volatile("ld.global.nc.L1::no_allocate.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(lo.x), "=r"(lo.y), "=r"(lo.z), "=r"(lo.w), "=r"(hi.x), "=r"(hi.y), "=r"(hi.z), "=r"(hi.w)
+               : "l"(p));
+}
+
 // TMA bulk prefetch of [p, p + bytes) into L2 (no registers, no completion):
 // p is rounded down and the end up to 16-byte boundaries; device allocations
 // carry 256 bytes of slack, so the rounded range stays inside them.

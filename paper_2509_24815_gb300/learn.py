@@ -151,7 +151,9 @@ def calibrate(index, weights: np.ndarray, queries: DeviceCSR, gt_scores, k: int,
     """Shifts the cut output's bias (logit units) so that the learned form's
     mean recall on held-out training queries reaches `target + margin`: the
     smallest such shift in [0, max_shift] (the least work), found by bisection
-    (recall grows with the shift).  Returns (weights, shift, recall)."""
+    (recall grows with the shift).  When even the largest shift stays below
+    target + margin (the collection's recall ceiling is near the target), the
+    goal drops to the target itself.  Returns (weights, shift, recall)."""
     base = dict(base_params or {})
     b3 = MLP_PARAMS - 2
     goal = target + margin
@@ -169,7 +171,11 @@ def calibrate(index, weights: np.ndarray, queries: DeviceCSR, gt_scores, k: int,
         return w0, 0.0, r0
     whi, rhi = run(max_shift)
     if rhi < goal:
-        return whi, max_shift, rhi
+        goal = target
+        if r0 >= goal:
+            return w0, 0.0, r0
+        if rhi < goal:
+            return whi, max_shift, rhi
     lo, hi, best = 0.0, max_shift, (whi, max_shift, rhi)
     for _ in range(iters):
         mid = 0.5 * (lo + hi)
