@@ -148,12 +148,14 @@ def predict(weights: np.ndarray, features: np.ndarray):
 
 def calibrate(index, weights: np.ndarray, queries: DeviceCSR, gt_scores, k: int, target: float,
               quantized: bool, base_params=None, margin: float = 0.005, max_shift: float = 12.0, iters: int = 12):
-    """Shifts the cut output's bias (logit units) so that the learned form's
-    mean recall on held-out training queries reaches `target + margin`: the
-    smallest such shift in [0, max_shift] (the least work), found by bisection
-    (recall grows with the shift).  When even the largest shift stays below
-    target + margin (the collection's recall ceiling is near the target), the
-    goal drops to the target itself.  Returns (weights, shift, recall)."""
+    """Shifts the output biases (logit units) so that the learned form's mean
+    recall on held-out training queries reaches `target + margin`: the cut
+    output's bias up by `shift` and the heap_factor output's bias down by the
+    same amount (both raise recall: more lists, less skipping); the smallest
+    such shift in [0, max_shift] (the least work), found by bisection.  When
+    even the largest shift stays below target + margin (the collection's
+    recall ceiling is near the target), the goal drops to the target itself.
+    Returns (weights, shift, recall)."""
     base = dict(base_params or {})
     b3 = MLP_PARAMS - 2
     goal = target + margin
@@ -161,6 +163,7 @@ def calibrate(index, weights: np.ndarray, queries: DeviceCSR, gt_scores, k: int,
     def run(shift):
         w = weights.copy()
         w[b3] += np.float32(shift)
+        w[b3 + 1] -= np.float32(shift)
         seismic_set_mlp(index, w)
         ids, sc = seismic_search(index, queries, search_params(k=k, cut=10, heap_factor=0.8, learned=True,
                                                                max_query_nnz=queries.max_row_nnz, **base))
