@@ -62,9 +62,9 @@ RECALL_TARGET = 0.9
 K = 10
 METRIC = "QPS at recall@10>=0.9 (batched Seismic search, fixed parameters)"
 # DRAM traffic of k_search per byte it executes (read + write), from one ncu capture of the current
-# kernel on the 300k-document workload, keyed by the row-value fetch (vsector); used to estimate a
-# full launch's traffic from its executed bytes.  A form without a capture reports null.
-TRAFFIC_PER_EXEC_BYTE = {0: 15.545494016e9 / 24.652337535e9}
+# kernel on the 300k-document workload (fp32 rows); used to estimate a full launch's traffic from its
+# executed bytes.  None (reported as null) when no capture of the current kernel exists.
+TRAFFIC_PER_EXEC_BYTE = 15.545494016e9 / 24.652337535e9
 
 
 def log(*a):
@@ -415,7 +415,6 @@ def main():
     ap.add_argument("--wave", type=int, default=16)
     ap.add_argument("--persistent", type=int, default=1)
     ap.add_argument("--shape", type=int, default=1, help="1 (or 0): CTA per query, 2: warp per query")
-    ap.add_argument("--vsector", type=int, default=0, help="1: fetch a chunk's whole value sector (fp32 rows)")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-compact", action="store_true", help="skip the fp16 forward-value form")
@@ -491,7 +490,7 @@ def main():
     def params(cut, hf, **kw):
         base = dict(k=K, cut=cut, heap_factor=hf, use_knn=bool(w["kappa"]), wave=args.wave, group=args.group,
                     cta_warps=args.cta_warps, persistent=bool(args.persistent), max_query_nnz=dq.max_row_nnz,
-                    shape=args.shape, no_prefetch=not args.prefetch, vsector=bool(args.vsector))
+                    shape=args.shape, no_prefetch=not args.prefetch)
         base.update(kw)
         return sz.search_params(**base)
 
@@ -537,7 +536,7 @@ def main():
     ok = [g for g in grid if g["recall"] >= RECALL_TARGET]
     best = max(ok, key=lambda g: g["qps"]) if ok else max(grid, key=lambda g: g["recall"])
     launch = dict(shape=args.shape, group=args.group, cta_warps=args.cta_warps, wave=args.wave,
-                  persistent=bool(args.persistent), no_prefetch=not args.prefetch, vsector=bool(args.vsector))
+                  persistent=bool(args.persistent), no_prefetch=not args.prefetch)
     p = params(best["cut"], best["heap_factor"])
     tuned = None
     if args.autotune:
@@ -554,8 +553,8 @@ def main():
         stream.synchronize()
         best["recall"] = recall_now()
         tuned = {"chosen": launch, "candidates": len(table),
-                 "table": [{x: t.get(x) for x in ("shape", "group", "cta_warps", "wave", "no_prefetch", "vsector",
-                                                   "ms", "recall")} for t in table]}
+                 "table": [{x: t.get(x) for x in ("shape", "group", "cta_warps", "wave", "no_prefetch", "ms",
+                                                   "recall")} for t in table]}
         log(f"autotune: {launch}, recall@10 {best['recall']:.4f}")
 
     # the method's bytes: the work counters of the sequential visiting order (wave 1) at the operating
@@ -635,7 +634,7 @@ def main():
     peak, peak_kind = peaks()
     sec = float(np.mean(per)) * 1e-3
     achieved = alg_bytes / sec / 1e9  # this rank's kernel, per launch
-    ratio = TRAFFIC_PER_EXEC_BYTE.get(int(bool(launch.get("vsector")))) if launch["shape"] != 2 else None
+    ratio = TRAFFIC_PER_EXEC_BYTE if launch["shape"] != 2 else None
     traffic = ratio * exec_bytes if ratio else None
     line = {
         "metric": METRIC,

@@ -122,10 +122,6 @@ typedef struct {
   uint32_t order;        /* persistent launches: 0 (default) runs queries grouped by their
                             largest term, so queries reading the same lists share L2; 1 runs
                             them in input order.  Results do not depend on it */
-  uint32_t vsector;      /* fp32 rows, CTA shape, group 1: 1 = fetch each row chunk's value
-                            sector with one 32-byte load beside its terms; 0 (default) = fetch
-                            a value only where its term is in the query.  A speed knob: same
-                            results */
 } seismic_search_params;
 
 /* Per-query work counters written by seismic_search when `stats` is non-NULL:

@@ -59,7 +59,7 @@ class SearchParams(ctypes.Structure):
                 ("use_knn", ctypes.c_int32), ("learned", ctypes.c_int32), ("wave", ctypes.c_uint32),
                 ("group", ctypes.c_uint32), ("cta_warps", ctypes.c_uint32), ("persistent", ctypes.c_uint32),
                 ("max_query_nnz", ctypes.c_uint32), ("hash_slots", ctypes.c_uint32), ("shape", ctypes.c_uint32),
-                ("no_prefetch", ctypes.c_int32), ("order", ctypes.c_uint32), ("vsector", ctypes.c_uint32)]
+                ("no_prefetch", ctypes.c_int32), ("order", ctypes.c_uint32)]
 
 
 class IndexInfo(ctypes.Structure):
@@ -207,11 +207,11 @@ def seismic_build(docs, lambda_=2000, beta=100, alpha=0.4, quantize_u8=False, se
 
 def search_params(k=10, cut=10, heap_factor=0.8, hf_mode=0, exhaustive=False, alpha_q=0.0, use_knn=False,
                   learned=False, wave=1, group=0, cta_warps=0, persistent=False, max_query_nnz=0,
-                  hash_slots=0, shape=0, no_prefetch=False, order=0, vsector=0) -> SearchParams:
+                  hash_slots=0, shape=0, no_prefetch=False, order=0) -> SearchParams:
     return SearchParams(int(k), int(cut), float(heap_factor), int(hf_mode), int(bool(exhaustive)), float(alpha_q),
                         int(bool(use_knn)), int(bool(learned)), int(wave), int(group), int(cta_warps),
                         int(bool(persistent)), int(max_query_nnz), int(hash_slots), int(shape),
-                        int(bool(no_prefetch)), int(order), int(bool(vsector)))
+                        int(bool(no_prefetch)), int(order))
 
 
 def seismic_search(index: Index, queries, params: SearchParams | None = None, *, ids_out=None, scores_out=None,

@@ -18,12 +18,11 @@ import numpy as np
 
 from . import DeviceCSR, search_params, seismic_info, seismic_search
 
-# (shape, group, cta_warps, wave, L2 row prefetch[, value sectors]): shape 1 =
-# one CTA per query (group 1: chunk-flattened scoring, else lane groups of that
-# width), 2 = one warp per query; value sectors: fetch a chunk's whole value
-# sector with its terms (fp32 rows, group 1)
+# (shape, group, cta_warps, wave, L2 row prefetch): shape 1 = one CTA per query
+# (group 1: chunk-flattened scoring, else lane groups of that width), 2 = one
+# warp per query
 DEFAULT_CANDIDATES = tuple(
-    [(1, 1, 8, v, pf, vs) for v in (4, 8, 16, 32) for pf in (False, True) for vs in (False, True)] +
+    [(1, 1, 8, v, pf) for v in (4, 8, 16, 32) for pf in (False, True)] +
     [(1, 1, 16, v, pf) for v in (8, 16) for pf in (False, True)] +
     [(1, 8, 8, v, pf) for v in (4, 16) for pf in (False, True)] +
     [(1, 16, 8, 16, True), (1, 8, 4, 16, True)] +
@@ -58,12 +57,10 @@ def autotune(index, queries: DeviceCSR, base: dict, recall_fn=None, min_recall: 
     ids = torch.empty((nq, k), dtype=torch.int32, device=queries.vals.device)
     sc = torch.empty((nq, k), dtype=torch.float32, device=queries.vals.device)
     table = []
-    for cand in candidates:
-        shape, g, w, v, pf = cand[:5]
-        vs = bool(cand[5]) if len(cand) > 5 else False
+    for shape, g, w, v, pf in candidates:
         if shape == 2 and k > 128:
             continue
-        launch = dict(shape=shape, group=g, cta_warps=w, wave=v, persistent=True, no_prefetch=not pf, vsector=vs)
+        launch = dict(shape=shape, group=g, cta_warps=w, wave=v, persistent=True, no_prefetch=not pf)
         p = search_params(max_query_nnz=queries.max_row_nnz, **dict(base, **launch))
         try:
             seismic_search(index, queries, p, ids_out=ids, scores_out=sc, stream=st)
@@ -84,14 +81,13 @@ def autotune(index, queries: DeviceCSR, base: dict, recall_fn=None, min_recall: 
         ms = float(np.median([ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(reps)]))
         table.append(dict(launch, ms=ms, qps=nq / ms * 1e3, recall=rec))
         if log:
-            log(f"  autotune shape={shape} group={g:2d} warps={w:2d} wave={v:2d} prefetch={int(pf)} vsector={int(vs)}: "
-                f"{ms:7.2f} ms"
+            log(f"  autotune shape={shape} group={g:2d} warps={w:2d} wave={v:2d} prefetch={int(pf)}: {ms:7.2f} ms"
                 + (f"  recall {rec:.4f}" if rec is not None else ""))
     ok = [t for t in table if "ms" in t and (min_recall is None or t["recall"] is None or t["recall"] >= min_recall)]
     if not ok:
         raise RuntimeError("autotune: no launch configuration ran and met the recall floor")
     top = min(ok, key=lambda t: t["ms"])
-    launch = {x: top[x] for x in ("shape", "group", "cta_warps", "wave", "persistent", "no_prefetch", "vsector")}
+    launch = {x: top[x] for x in ("shape", "group", "cta_warps", "wave", "persistent", "no_prefetch")}
     if cache:
         data = {}
         if os.path.exists(cache):

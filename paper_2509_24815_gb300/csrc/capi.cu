@@ -286,7 +286,6 @@ int search_ws(seismic_index *ix, Workspace *w, const seismic_csr *queries, const
   const uint32_t nw = p->cta_warps ? p->cta_warps : 8, group = p->group ? p->group : (p->shape == 2 ? 8 : 1);
   a.sum_absmax = ix->sum_absmax;
   a.prefetch = p->no_prefetch ? 0u : 256u;
-  a.vsector = p->vsector ? 1u : 0u;
   const bool warp_shape0 = p->shape == 2;
   if (p->order == 0 && nq > 1 && (a.persistent || warp_shape0)) {
     if ((rc = w->perm.ensure((size_t)nq * 12))) return rc;

@@ -126,7 +126,6 @@ extern "C" int seismic_search_noalloc(seismic_index *ix, const seismic_csr *quer
   a.CAND = 256;
   a.sum_absmax = ix->sum_absmax;
   a.prefetch = p->no_prefetch ? 0u : 256u;
-  a.vsector = p->vsector ? 1u : 0u;
   a.perm = nullptr;
   a.flat = group == 1 ? 1u : 0u;
   const size_t smem = search_layout(a, nw);

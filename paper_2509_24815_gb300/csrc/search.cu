@@ -168,21 +168,29 @@ __device__ void merge_candidates(const SearchArgs &a, Smem &s, Shared &sh) {
   const int tid = threadIdx.x;
   const uint32_t m = sh.ncand, cnt = sh.count, k = a.k;
   if (m == 0) return;  // uniform: every thread read the same ncand after the barrier
-  const bool dupcheck = sh.hash_full != 0u;
-  for (uint32_t i = tid; i < m; i += NT) {
-    const uint32_t id = s.cand_id()[i];
-    uint8_t ok = 1;
-    for (uint32_t j = 0; j < cnt; j++)
-      if (s.tk_id()[j] == id) { ok = 0; break; }
-    if (ok && dupcheck)
-      for (uint32_t j = 0; j < i; j++)
-        if (s.cand_id()[j] == id) { ok = 0; break; }
-    s.cand_ok()[i] = ok;
-    if (ok) atomicAdd(&sh.nvalid, 1u);
+  // With the global seen bitmap a document becomes fresh once per query, so no
+  // candidate repeats a heap entry or another candidate.  The bounded hash set
+  // may score a document again when it is crowded: there repeats are dropped.
+  const bool check = s.seen == nullptr;
+  uint32_t nvalid = m;
+  if (check) {
+    const bool dupcheck = sh.hash_full != 0u;
+    for (uint32_t i = tid; i < m; i += NT) {
+      const uint32_t id = s.cand_id()[i];
+      uint8_t ok = 1;
+      for (uint32_t j = 0; j < cnt; j++)
+        if (s.tk_id()[j] == id) { ok = 0; break; }
+      if (ok && dupcheck)
+        for (uint32_t j = 0; j < i; j++)
+          if (s.cand_id()[j] == id) { ok = 0; break; }
+      s.cand_ok()[i] = ok;
+      if (ok) atomicAdd(&sh.nvalid, 1u);
+    }
+    __syncthreads();
+    nvalid = sh.nvalid;
   }
-  __syncthreads();
   for (uint32_t i = tid; i < m; i += NT) {
-    if (!s.cand_ok()[i]) continue;
+    if (check && !s.cand_ok()[i]) continue;
     const float sc = s.cand_s()[i];
     const uint32_t id = s.cand_id()[i];
     uint32_t lo = 0, hi = cnt;  // topk entries better than (sc, id)
@@ -192,7 +200,7 @@ __device__ void merge_candidates(const SearchArgs &a, Smem &s, Shared &sh) {
     }
     uint32_t r = lo;
     for (uint32_t j = 0; j < m; j++)
-      if (s.cand_ok()[j] && better(s.cand_s()[j], s.cand_id()[j], sc, id)) r++;
+      if ((!check || s.cand_ok()[j]) && better(s.cand_s()[j], s.cand_id()[j], sc, id)) r++;
     if (r < k) { s.tmp_s()[r] = sc; s.tmp_id()[r] = id; }
   }
   for (uint32_t i = tid; i < cnt; i += NT) {
@@ -200,13 +208,13 @@ __device__ void merge_candidates(const SearchArgs &a, Smem &s, Shared &sh) {
     const uint32_t id = s.tk_id()[i];
     uint32_t r = i;
     for (uint32_t j = 0; j < m; j++)
-      if (s.cand_ok()[j] && better(s.cand_s()[j], s.cand_id()[j], sc, id)) r++;
+      if ((!check || s.cand_ok()[j]) && better(s.cand_s()[j], s.cand_id()[j], sc, id)) r++;
     if (r < k) { s.tmp_s()[r] = sc; s.tmp_id()[r] = id; }
   }
   __syncthreads();
-  const uint32_t nc = min(k, cnt + sh.nvalid);
+  // nc comes from registers, so thread 0 may reset the counters in this phase
+  const uint32_t nc = min(k, cnt + nvalid);
   for (uint32_t i = tid; i < nc; i += NT) { s.tk_s()[i] = s.tmp_s()[i]; s.tk_id()[i] = s.tmp_id()[i]; }
-  __syncthreads();
   if (tid == 0) { sh.count = nc; sh.ncand = 0; sh.nvalid = 0; }
   __syncthreads();
 }
@@ -266,10 +274,12 @@ __device__ void eval_wave(const SearchArgs &a, Smem &s, Shared &sh, uint32_t n, 
   merge_candidates<NT>(a, s, sh);
 }
 
-// v[0..n) -> exclusive prefix sums, v[n] = the total (n <= 32 * NT).  Starts
-// and ends with a barrier-separated phase; every thread must call it.  When
-// map is given and the total is at most cap, also writes map[v[i] .. v[i+1])
-// = i (the owner of each unit, i < 256).
+// v[0..n) -> exclusive prefix sums, v[n] = the total.  Thread t takes a
+// contiguous range of ceil(n / NT) elements; warps scan their threads' sums
+// with shuffles and every thread adds the totals of the warps before it, so
+// the scan costs two barriers.  Every thread must call it (after a barrier
+// that published v).  When map is given and the total is at most cap, also
+// writes map[v[i] .. v[i+1]) = i (the owner of each unit, i < 256).
 template <int NT>
 __device__ uint32_t block_exclusive_scan(uint32_t *v, uint32_t n, uint32_t *wtmp, uint8_t *map = nullptr,
                                          uint32_t cap = 0) {
@@ -286,18 +296,14 @@ __device__ uint32_t block_exclusive_scan(uint32_t *v, uint32_t n, uint32_t *wtmp
   }
   if (lane == 31) wtmp[warp] = x;
   __syncthreads();
-  if (warp == 0) {
-    uint32_t w = lane < nw ? wtmp[lane] : 0;
+  uint32_t before = 0, total = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += y;
-    }
-    if (lane < nw) wtmp[lane] = w;
+  for (int w = 0; w < nw; w++) {
+    const uint32_t t = wtmp[w];
+    before += w < warp ? t : 0u;
+    total += t;
   }
-  __syncthreads();
-  uint32_t run = (warp ? wtmp[warp - 1] : 0) + x - sum;
-  const uint32_t total = wtmp[nw - 1];
+  uint32_t run = before + x - sum;
   const bool fill = map != nullptr && total <= cap;
   for (uint32_t i = lo; i < hi; i++) {
     const uint32_t c = v[i];
@@ -320,7 +326,7 @@ __device__ uint32_t block_exclusive_scan(uint32_t *v, uint32_t n, uint32_t *wtmp
 // no row reads.  fp32 rows: a chunk's values (one 32-byte sector) are read
 // only where a term is in the query (4-byte read-only loads; most chunks of a
 // row miss).  fp16 rows: a chunk is one sector, terms and values read together.
-template <int NT, bool FP16, bool VSEC, class Src>
+template <int NT, bool FP16, class Src>
 __device__ __forceinline__ void eval_wave_flat(const SearchArgs &a, Smem &s, Shared &sh, uint32_t n, const Src &src,
                                                int knn_stage) {
   constexpr int U = 2;
@@ -383,7 +389,7 @@ __device__ __forceinline__ void eval_wave_flat(const SearchArgs &a, Smem &s, Sha
     for (uint32_t j = tid; j < total; j += NT * U) {
       // a row holds its chunks' terms (16 B each), then their values (32 B each):
       // the terms are read first and a value only where the term is in the query
-      uint4 t[U], vh[U], vl[U];
+      uint4 t[U], vh[U];
       const float *vp[U];
 #pragma unroll
       for (int u = 0; u < U; u++) {  // past the end: the last chunk again (unconditional loads stay in registers)
@@ -397,7 +403,6 @@ __device__ __forceinline__ void eval_wave_flat(const SearchArgs &a, Smem &s, Sha
             ldg_na_v8(chunk_terms(rec, o, true), t[u], vh[u]);  // the chunk's sector: terms, then halves
           } else {
             t[u] = ldg_na(chunk_terms(rec, o, false));
-            if (VSEC) ldg_na_v8(vp[u], vh[u], vl[u]);
           }
         }
       }
@@ -406,7 +411,7 @@ __device__ __forceinline__ void eval_wave_flat(const SearchArgs &a, Smem &s, Sha
         const uint32_t jj = j + u * NT;
         if (jj < total) {
           const uint32_t tw[4] = {t[u].x, t[u].y, t[u].z, t[u].w};
-          const uint32_t hw[8] = {vh[u].x, vh[u].y, vh[u].z, vh[u].w, vl[u].x, vl[u].y, vl[u].z, vl[u].w};
+          const uint32_t hw[4] = {vh[u].x, vh[u].y, vh[u].z, vh[u].w};
           float acc = 0.0f;
 #pragma unroll
           for (int e = 0; e < 8; e++) {  // absent terms (most) cost one shared load and no value read
@@ -415,7 +420,6 @@ __device__ __forceinline__ void eval_wave_flat(const SearchArgs &a, Smem &s, Sha
             if ((w >> sh5) & 1u) {
               float v;
               if (FP16) v = __half2float(__ushort_as_half((unsigned short)((e & 1) ? (hw[e >> 1] >> 16) : (hw[e >> 1] & 0xFFFFu))));
-              else if (VSEC) v = __uint_as_float(hw[e]);
               else v = __ldg(vp[u] + e);
               acc = fmaf(qv[qr[tt >> 5] + __popc(w & ((1u << sh5) - 1u))], v, acc);
             }
@@ -447,9 +451,8 @@ template <int G, int NT, class Src>
 __device__ __forceinline__ void eval(const SearchArgs &a, Smem &s, Shared &sh, uint32_t n, const Src &src,
                                      int knn_stage) {
   if constexpr (G == 1) {
-    if (a.fp16) eval_wave_flat<NT, true, false>(a, s, sh, n, src, knn_stage);
-    else if (a.vsector) eval_wave_flat<NT, false, true>(a, s, sh, n, src, knn_stage);
-    else eval_wave_flat<NT, false, false>(a, s, sh, n, src, knn_stage);
+    if (a.fp16) eval_wave_flat<NT, true>(a, s, sh, n, src, knn_stage);
+    else eval_wave_flat<NT, false>(a, s, sh, n, src, knn_stage);
   } else {
     eval_wave<G, NT>(a, s, sh, n, src, knn_stage);
   }

@@ -62,10 +62,6 @@ struct SearchArgs {
   // CTA kernel, group 1: documents are scored chunk by chunk by all threads
   // of the CTA (a wave's chunks laid end to end, then summed per document)
   uint32_t flat;
-  // fp32 rows, group 1: 1 = read each chunk's whole value sector with one
-  // 32-byte load together with its terms (one dependent round trip per chunk
-  // instead of two); 0 = read a value only where its term is in the query
-  uint32_t vsector;
   // shared-memory layout
   uint32_t W, QN, BMAX, BPOW2, HS, CAND, CAPC;
   uint32_t off_qbits, off_qrank, off_qval, off_qterm, off_cut, off_aq, off_part, off_keys, off_clo, off_chi,

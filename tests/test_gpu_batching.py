@@ -94,20 +94,3 @@ def test_cuda_graph_replay_equals_direct_launch(sz, small, small_built, use_knn)
     if use_knn:
         sz.seismic_set_knn(ix, np.zeros((small["docs"].n_rows, 0), dtype=np.uint32))
 
-
-@pytest.mark.parametrize("quant", [True, False])
-def test_value_sector_loads_change_nothing(sz, small, small_built, quant):
-    """Fetching a chunk's whole value sector (vsector = 1) instead of one value
-    per query hit reads the same fp32 values and adds them in the same order:
-    ids and scores are bit-identical."""
-    import torch
-    ix, _ = small_built[quant]
-    dq = sz.DeviceCSR.from_host(small["queries"])
-    out = []
-    for vs in (0, 1):
-        p = sz.search_params(k=10, cut=5, heap_factor=0.9, wave=4, persistent=True, vsector=vs,
-                             max_query_nnz=dq.max_row_nnz)
-        i, s = sz.seismic_search(ix, dq, p)
-        torch.cuda.synchronize()
-        out.append((i.cpu(), s.cpu()))
-    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
