@@ -312,12 +312,6 @@ size_t asg_smem_bytes(uint32_t dim) {
          (size_t)(kAsgMaxEnt + 1) * 2 + W * 2 + kAsgMaxEnt + 16;
 }
 
-struct Mss {
-  float a;
-  uint16_t t;
-  uint32_t i;
-};
-
 }  // namespace
 
 int validate_host_csr(const seismic_csr *m, const char *what, uint32_t dim_expect) {
@@ -413,15 +407,41 @@ int build_index(const seismic_csr *docs, const seismic_build_params *bp, seismic
   std::vector<uint32_t> fdoc(ix->nnz);
   std::vector<float> fval(ix->nnz);
   {
-    for (uint64_t p = 0; p < ix->nnz; p++) fptr[D.t[p] + 1]++;
-    for (uint32_t t = 0; t < d; t++) fptr[t + 1] += fptr[t];
-    std::vector<uint64_t> cur(fptr.begin(), fptr.end() - 1);
-    for (uint64_t i = 0; i < D.n; i++)
-      for (uint64_t p = D.ip[i]; p < D.ip[i + 1]; p++) {
-        uint64_t o = cur[D.t[p]]++;
-        fdoc[o] = (uint32_t)i;
-        fval[o] = D.v[p];
+    // a counting sort in parallel: each worker counts, then places, the
+    // postings of its own contiguous range of documents; a term's postings from
+    // earlier ranges come first, so every list is in ascending document order
+    const uint64_t parts = std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)T, D.n));
+    std::vector<std::vector<uint64_t>> hist(parts, std::vector<uint64_t>(d, 0));
+    auto range = [&](uint64_t r, uint64_t &lo, uint64_t &hi) {
+      lo = D.n * r / parts;
+      hi = D.n * (r + 1) / parts;
+    };
+    parallel_for((int64_t)parts, T, [&](int64_t r, int) {
+      uint64_t lo, hi;
+      range((uint64_t)r, lo, hi);
+      for (uint64_t p = D.ip[lo]; p < D.ip[hi]; p++) hist[r][D.t[p]]++;
+    });
+    uint64_t run = 0;
+    for (uint32_t t = 0; t < d; t++) {
+      fptr[t] = run;
+      for (uint64_t r = 0; r < parts; r++) {
+        const uint64_t c = hist[r][t];
+        hist[r][t] = run;  // this range's first slot in list t
+        run += c;
       }
+    }
+    fptr[d] = run;
+    parallel_for((int64_t)parts, T, [&](int64_t r, int) {
+      uint64_t lo, hi;
+      range((uint64_t)r, lo, hi);
+      std::vector<uint64_t> &cur = hist[r];
+      for (uint64_t i = lo; i < hi; i++)
+        for (uint64_t p = D.ip[i]; p < D.ip[i + 1]; p++) {
+          const uint64_t o = cur[D.t[p]]++;
+          fdoc[o] = (uint32_t)i;
+          fval[o] = D.v[p];
+        }
+    });
   }
   if (bp->keep_full_lists) {
     if (ix->nnz > 0xFFFFFFFFull) return fail(SEISMIC_EINVAL, "keep_full_lists: more than 2^32 nonzeros");
@@ -586,7 +606,7 @@ int build_index(const seismic_csr *docs, const seismic_build_params *bp, seismic
     std::vector<std::vector<float>> mx(T, std::vector<float>(d));
     std::vector<std::vector<uint32_t>> cn(T, std::vector<uint32_t>(d, 0));
     std::vector<std::vector<uint16_t>> touched(T, std::vector<uint16_t>(d));
-    std::vector<std::vector<Mss>> ms(T, std::vector<Mss>(d));
+    std::vector<std::vector<uint64_t>> ms(T, std::vector<uint64_t>(d));
     parallel_for(d, T, [&](int64_t t, int tid) {
       ListSum &L = ls[t];
       uint32_t g0 = bptr[t], g1 = bptr[t + 1];
@@ -596,7 +616,7 @@ int build_index(const seismic_csr *docs, const seismic_build_params *bp, seismic
       float *mxx = mx[tid].data();
       uint32_t *cc = cn[tid].data();
       uint16_t *tch = touched[tid].data();
-      Mss *buf = ms[tid].data();
+      uint64_t *buf = ms[tid].data();
       for (uint32_t g = g0; g < g1; g++) {
         uint32_t bs = bdptr[g + 1] - bdptr[g], nt = 0;
         for (uint32_t m = bdptr[g]; m < bdptr[g + 1]; m++) {
@@ -613,41 +633,48 @@ int build_index(const seismic_csr *docs, const seismic_build_params *bp, seismic
             cc[s]++;
           }
         }
+        // the summary's nonzero coordinates as keys that sort by (|phi| desc, term asc):
+        // the bits of |phi| (a non-negative float orders like its bits) complemented,
+        // then the term; phi itself stays in mxx[term] for the rest of this block
         uint32_t ne = 0;
         for (uint32_t i = 0; i < nt; i++) {
           uint16_t s = tch[i];
           float phi = mxx[s];
-          if (cc[s] < bs && phi < 0.0f) phi = 0.0f;  // members without the term contribute 0
+          if (cc[s] < bs && phi < 0.0f) mxx[s] = phi = 0.0f;  // members without the term contribute 0
           cc[s] = 0;
           if (phi != 0.0f) {
-            buf[ne].a = std::fabs(phi);
-            buf[ne].t = s;
-            buf[ne].i = *reinterpret_cast<uint32_t *>(&phi);
-            ne++;
+            uint32_t ab;
+            const float a = std::fabs(phi);
+            std::memcpy(&ab, &a, 4);
+            buf[ne++] = ((uint64_t)(0xFFFFFFFFu - ab) << 16) | s;
           }
         }
-        std::sort(buf, buf + ne, [](const Mss &x, const Mss &y) {
-          if (x.a != y.a) return x.a > y.a;
-          return x.t < y.t;
-        });
+        std::sort(buf, buf + ne);
+        auto mass = [](uint64_t key) {
+          const uint32_t ab = 0xFFFFFFFFu - (uint32_t)(key >> 16);
+          float a;
+          std::memcpy(&a, &ab, 4);
+          return (double)a;
+        };
         double total = 0.0;
-        for (uint32_t i = 0; i < ne; i++) total += (double)buf[i].a;
+        for (uint32_t i = 0; i < ne; i++) total += mass(buf[i]);
         double target = alpha * total, c = 0.0;
         uint32_t keep = ne;
         for (uint32_t i = 0; i < ne; i++) {
-          c += (double)buf[i].a;
+          c += mass(buf[i]);
           if (c >= target) {
             keep = i + 1;
             break;
           }
         }
-        std::sort(buf, buf + keep, [](const Mss &x, const Mss &y) { return x.t < y.t; });
+        for (uint32_t i = 0; i < keep; i++) buf[i] &= 0xFFFFull;  // the kept terms, to sort ascending
+        std::sort(buf, buf + keep);
         float lo = INFINITY, hi = -INFINITY;
         size_t base = L.term.size();
         for (uint32_t i = 0; i < keep; i++) {
-          float v;
-          std::memcpy(&v, &buf[i].i, 4);
-          L.term.push_back(buf[i].t);
+          const uint16_t tt = (uint16_t)buf[i];
+          const float v = mxx[tt];
+          L.term.push_back(tt);
           L.val.push_back(v);
           lo = std::min(lo, v);
           hi = std::max(hi, v);
@@ -694,9 +721,11 @@ int build_index(const seismic_csr *docs, const seismic_build_params *bp, seismic
     ix->sum_absmax = (float)(mx * 1.001 + 1e-30);
   }
   {
-    std::vector<uint16_t> sterm(nsum);
-    std::vector<float> sval(nsum), bm(nblk), bsz(nblk);
-    std::vector<uint8_t> scode(quant ? nsum : 0);
+    // the block-major copies are kept only for export
+    const bool keep_bm = bp->keep_block_summaries != 0;
+    std::vector<uint16_t> sterm(keep_bm ? nsum : 0);
+    std::vector<float> sval(keep_bm ? nsum : 0), bm(nblk), bsz(nblk);
+    std::vector<uint8_t> scode(keep_bm && quant ? nsum : 0);
     std::vector<uint16_t> cblk(nsum);
     std::vector<uint8_t> ccode(quant ? nsum : 0);
     std::vector<float> cval(quant ? 0 : nsum);
@@ -723,7 +752,7 @@ int build_index(const seismic_csr *docs, const seismic_build_params *bp, seismic
         bm[g0 + b] = L.m[b];
         bsz[g0 + b] = L.size[b];
       }
-      if (!L.term.empty()) {
+      if (keep_bm && !L.term.empty()) {
         std::memcpy(&sterm[base], L.term.data(), L.term.size() * 2);
         std::memcpy(&sval[base], L.val.data(), L.val.size() * 4);
         if (quant) std::memcpy(&scode[base], L.code.data(), L.code.size());

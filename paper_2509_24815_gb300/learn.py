@@ -154,7 +154,8 @@ def calibrate(index, weights: np.ndarray, queries: DeviceCSR, gt_scores, k: int,
     same amount (both raise recall: more lists, less skipping); the smallest
     such shift in [0, max_shift] (the least work), found by bisection.  When
     even the largest shift stays below target + margin (the collection's
-    recall ceiling is near the target), the goal drops to the target itself.
+    recall ceiling is near the target), the goal drops to target + 0.002, or to
+    the target itself.
     Returns (weights, shift, recall)."""
     base = dict(base_params or {})
     b3 = MLP_PARAMS - 2
@@ -174,7 +175,9 @@ def calibrate(index, weights: np.ndarray, queries: DeviceCSR, gt_scores, k: int,
         return w0, 0.0, r0
     whi, rhi = run(max_shift)
     if rhi < goal:
-        goal = target
+        # the ceiling is close to the target: the largest reachable of a small
+        # margin above it and the target itself
+        goal = target + 0.002 if rhi >= target + 0.002 else target
         if r0 >= goal:
             return w0, 0.0, r0
         if rhi < goal:
