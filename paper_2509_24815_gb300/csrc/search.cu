@@ -125,7 +125,6 @@ struct Smem {
   __device__ __forceinline__ uint32_t *fc0() const { return reinterpret_cast<uint32_t *>(g_sm + a.off_fc0); }
   __device__ __forceinline__ uint32_t *fpre() const { return reinterpret_cast<uint32_t *>(g_sm + a.off_fpre); }
   __device__ __forceinline__ uint8_t *cmap() const { return reinterpret_cast<uint8_t *>(g_sm + a.off_cmap); }
-  __device__ __forceinline__ uint4 *frec() const { return reinterpret_cast<uint4 *>(g_sm + a.off_frec); }
 };
 
 struct Shared {
@@ -280,11 +279,10 @@ __device__ void eval_wave(const SearchArgs &a, Smem &s, Shared &sh, uint32_t n, 
 // with shuffles and every thread adds the totals of the warps before it, so
 // the scan costs two barriers.  Every thread must call it (after a barrier
 // that published v).  When map is given and the total is at most cap, also
-// writes map[v[i] .. v[i+1]) = i (the owner of each unit, i < 256).  When rec
-// is given, also writes rec[i] = (v[i], tag[i], count of i, 0).
+// writes map[v[i] .. v[i+1]) = i (the owner of each unit, i < 256).
 template <int NT>
 __device__ uint32_t block_exclusive_scan(uint32_t *v, uint32_t n, uint32_t *wtmp, uint8_t *map = nullptr,
-                                         uint32_t cap = 0, uint4 *rec = nullptr, const uint32_t *tag = nullptr) {
+                                         uint32_t cap = 0) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int nw = NT / 32;
   const uint32_t per = (n + NT - 1) / NT, lo = min(n, tid * per), hi = min(n, lo + per);
@@ -310,7 +308,6 @@ __device__ uint32_t block_exclusive_scan(uint32_t *v, uint32_t n, uint32_t *wtmp
   for (uint32_t i = lo; i < hi; i++) {
     const uint32_t c = v[i];
     v[i] = run;
-    if (rec) rec[i] = make_uint4(run, tag[i], c, 0u);
     if (fill)
       for (uint32_t u = 0; u < c; u++) map[run + u] = (uint8_t)i;
     run += c;
@@ -367,7 +364,7 @@ __device__ __forceinline__ void eval_wave_flat(const SearchArgs &a, Smem &s, Sha
   }
   __syncthreads();
   // the chunk map of a wave that fits one pass is written by the scan itself
-  const uint32_t all = block_exclusive_scan<NT>(s.fpre(), n, sh.wtmp, s.cmap(), a.CAPC, s.frec(), s.fc0());
+  const uint32_t all = block_exclusive_scan<NT>(s.fpre(), n, sh.wtmp, s.cmap(), a.CAPC);
   const uint32_t *qb = s.qbits();
   const uint16_t *qr = s.qrank();
   const float *qv = s.qval();
@@ -398,9 +395,9 @@ __device__ __forceinline__ void eval_wave_flat(const SearchArgs &a, Smem &s, Sha
       for (int u = 0; u < U; u++) {  // past the end: the last chunk again (unconditional loads stay in registers)
         const uint32_t jj = min(j + u * NT, total - 1u);
         {
-          const uint4 r = s.frec()[s.cmap()[jj]];  // (first chunk, row unit, chunks)
-          const uint32_t nch = r.z, o = base + jj - r.x;
-          const uint8_t *rec = a.fwd_data + (size_t)r.y * kUnitBytes;
+          const uint32_t i = s.cmap()[jj], p0 = s.fpre()[i];
+          const uint32_t nch = s.fpre()[i + 1] - p0, o = base + jj - p0;
+          const uint8_t *rec = a.fwd_data + (size_t)s.fc0()[i] * kUnitBytes;
           vp[u] = reinterpret_cast<const float *>(chunk_vals(rec, nch, o, FP16));
           if (FP16) {
             ldg_na_v8(chunk_terms(rec, o, true), t[u], vh[u]);  // the chunk's sector: terms, then halves
@@ -814,7 +811,6 @@ size_t search_layout(SearchArgs &a, uint32_t nw) {
     a.off_fc0 = take(a.CAND * 4);
     a.off_fpre = take((a.CAND + 1) * 4);
     a.off_cmap = take(a.CAPC);
-    a.off_frec = take(a.CAND * 16);
   }
   return o;
 }

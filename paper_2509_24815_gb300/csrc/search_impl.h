@@ -66,7 +66,7 @@ struct SearchArgs {
   uint32_t W, QN, BMAX, BPOW2, HS, CAND, CAPC;
   uint32_t off_qbits, off_qrank, off_qval, off_qterm, off_cut, off_aq, off_part, off_keys, off_clo, off_chi,
       off_hash, off_tk_s, off_tk_id, off_tmp_s, off_tmp_id, off_cand_s, off_cand_id, off_cand_ok,
-      off_fdoc, off_fc0, off_fpre, off_cmap, off_frec, off_bptr;
+      off_fdoc, off_fc0, off_fpre, off_cmap, off_bptr;
 };
 
 constexpr uint32_t kMaxWave = 64;  // blocks per wave (CTA kernel)
