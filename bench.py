@@ -446,6 +446,7 @@ def main():
     from paper_2509_24815_gb300 import autotune, metrics
 
     t_all = time.time()
+    os.environ.setdefault("SEISMIC_BUILD_TRACE", "1")  # the index build's phase times go to the log
     docs, queries = make_data(w)
     t = time.time()
     ix = sz.seismic_build(docs, lambda_=w["lam"], beta=w["beta"], alpha=w["alpha"], quantize_u8=w["quant"], seed=0,
