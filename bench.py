@@ -62,9 +62,10 @@ RECALL_TARGET = 0.9
 K = 10
 METRIC = "QPS at recall@10>=0.9 (batched Seismic search, fixed parameters)"
 # DRAM traffic of k_search per byte it executes (read + write), from one ncu capture of the current
-# kernel on the 300k-document workload (fp32 rows); used to estimate a full launch's traffic from its
-# executed bytes.  None (reported as null) when no capture of the current kernel exists.
-TRAFFIC_PER_EXEC_BYTE = 15.545494016e9 / 24.652337535e9
+# kernel on the 300k-document workload (fp32 rows, wave 8), keyed by the L2 row prefetch (which
+# brings whole rows in); used to estimate a full launch's traffic from its executed bytes.  A form
+# without a capture of the current kernel reports null.
+TRAFFIC_PER_EXEC_BYTE = {False: None, True: None}
 
 
 def log(*a):
@@ -635,7 +636,7 @@ def main():
     peak, peak_kind = peaks()
     sec = float(np.mean(per)) * 1e-3
     achieved = alg_bytes / sec / 1e9  # this rank's kernel, per launch
-    ratio = TRAFFIC_PER_EXEC_BYTE if launch["shape"] != 2 else None
+    ratio = TRAFFIC_PER_EXEC_BYTE.get(not launch["no_prefetch"]) if launch["shape"] != 2 else None
     traffic = ratio * exec_bytes if ratio else None
     line = {
         "metric": METRIC,
@@ -654,8 +655,8 @@ def main():
                      "alg_bytes_per_launch": alg_bytes, "alg_bytes_basis": "work counters of the sequential "
                      "visiting order (wave 1) at the operating point",
                      "executed_bytes_per_launch": exec_bytes, "executed_frac": exec_bytes / sec / 1e9 / peak,
-                     "traffic_basis": ("ncu DRAM bytes per executed byte on the 300k-document workload, scaled by "
-                                       "this launch's executed bytes") if traffic else None,
+                     "traffic_basis": ("ncu DRAM bytes per executed byte on the 300k-document workload (same "
+                                       "prefetch setting), scaled by this launch's executed bytes") if traffic else None,
                      "traffic_over_alg": (traffic / alg_bytes) if traffic else None},
         "queue_occupancy": occupancy,
         "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
