@@ -121,7 +121,9 @@ typedef struct {
                             (a speed knob; results are the same) */
   uint32_t order;        /* persistent launches: 0 (default) runs queries grouped by their
                             largest term, so queries reading the same lists share L2; 1 runs
-                            them in input order.  Results do not depend on it */
+                            them in input order; 2 runs the queries that traverse the most
+                            lists first, grouped by largest term within each count, so the
+                            queue ends on its cheapest queries.  Results do not depend on it */
 } seismic_search_params;
 
 /* Per-query work counters written by seismic_search when `stats` is non-NULL:

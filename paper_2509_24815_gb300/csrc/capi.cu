@@ -69,20 +69,29 @@ uint32_t knn_bits_for(uint64_t n) {
 
 // Work-queue order of a persistent search: queries sorted by their largest
 // term (the first list they traverse), so queries that read the same lists,
-// blocks and rows run at the same time and share them through L2.  Results do
-// not depend on the order.
+// blocks and rows run at the same time and share them through L2.  With
+// longest_first, queries that traverse more lists (min(nonzeros, cut), the
+// per-query cut when learned) come first and the largest term orders each
+// such class, so the queue ends on its cheapest queries.  Results do not
+// depend on the order.
 __global__ void k_order_keys(const uint64_t *ip, const uint16_t *t, const float *v, uint32_t nq,
-                             unsigned long long *keys) {
+                             unsigned long long *keys, int longest_first, uint32_t cut, const uint32_t *q_cut) {
   const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nq) return;
   float bv = -INFINITY;
-  uint32_t bt = 0xFFFFu;
+  uint32_t bt = 0xFFFFu, nz = 0;
   for (uint64_t p = ip[q]; p < ip[q + 1]; p++) {
     const float x = v[p];
     const uint32_t tt = t[p];
+    nz += x != 0.0f;
     if (x != 0.0f && (x > bv || (x == bv && tt < bt))) { bv = x; bt = tt; }
   }
-  keys[q] = ((unsigned long long)bt << 32) | q;
+  unsigned long long key = ((unsigned long long)bt << 32) | q;
+  if (longest_first) {
+    const uint32_t lists = min(nz, q_cut ? q_cut[q] : cut);
+    key |= (unsigned long long)(0xFFFFu - min(lists, 0xFFFFu)) << 48;
+  }
+  keys[q] = key;
 }
 
 constexpr uint32_t kOrderChunk = 8192;
@@ -287,11 +296,12 @@ int search_ws(seismic_index *ix, Workspace *w, const seismic_csr *queries, const
   a.sum_absmax = ix->sum_absmax;
   a.prefetch = p->no_prefetch ? 0u : 256u;
   const bool warp_shape0 = p->shape == 2;
-  if (p->order == 0 && nq > 1 && (a.persistent || warp_shape0)) {
+  if ((p->order == 0 || p->order == 2) && nq > 1 && (a.persistent || warp_shape0)) {
     if ((rc = w->perm.ensure((size_t)nq * 12))) return rc;
     unsigned long long *keys = w->perm.as<unsigned long long>();
     uint32_t *perm = reinterpret_cast<uint32_t *>(keys + nq);
-    k_order_keys<<<(nq + 255) / 256, 256, 0, st>>>(q.ip, q.t, q.v, nq, keys);
+    k_order_keys<<<(nq + 255) / 256, 256, 0, st>>>(q.ip, q.t, q.v, nq, keys, p->order == 2 ? 1 : 0,
+                                                     p->alpha_q > 0.0f ? 0xFFFFu : p->cut, a.q_cut);
     SZ_CUDA(cudaGetLastError());
     static std::atomic<uint64_t> attr{0};
     if ((rc = set_smem_limit_once(attr, (const void *)k_order_sort, kOrderChunk * 8))) return rc;
