@@ -313,6 +313,9 @@ def learned_eval(args, w, sz, ix, dq, gt_sc, stream, time_runs, launch):
             "label_grid": {"cut": list(kw.get("grid_cut", learn.GRID_CUT)), "hf": list(kw.get("grid_hf", learn.GRID_HF))},
             "label_target_recall": args.learn_target, "fit_seconds": t_fit,
             "final_loss": res["trace"][-1][1], "label_mean_recall": res["label_recall"],
+            "label_mean_bytes_per_query": res["label_bytes"],
+            "label_grid_bytes_per_query": {f"cut={c} hf={h}": float(np.mean(b)) for c, h, _, b in res["table"]},
+            "label_grid_recall": {f"cut={c} hf={h}": float(np.mean(r)) for c, h, r, _ in res["table"]},
             "calibration_shift": res["calib_shift"], "validation_recall": res["val_recall"],
             "fixed_fine_grid": fine}
 
