@@ -94,3 +94,27 @@ def test_cuda_graph_replay_equals_direct_launch(sz, small, small_built, use_knn)
     if use_knn:
         sz.seismic_set_knn(ix, np.zeros((small["docs"].n_rows, 0), dtype=np.uint32))
 
+
+
+@pytest.mark.parametrize("learned", [False, True])
+def test_work_queue_orders_change_nothing(sz, small, small_built, learned):
+    """Orders 0 (largest term), 1 (input order) and 2 (most lists first) only
+    change which CTA takes which query and when: ids and scores are
+    bit-identical, with fixed and with learned per-query parameters."""
+    import torch
+    from paper_2509_24815_gb300 import learn
+    ix, _ = small_built[True]
+    dq = sz.DeviceCSR.from_host(small["queries"])
+    if learned:
+        w = learn.init_weights(2)
+        w[-2 - 2 * 64:-2] = np.random.default_rng(1).standard_normal(2 * 64).astype(np.float32) * 0.003
+        sz.seismic_set_mlp(ix, w)
+    out = []
+    for order in (0, 1, 2):
+        p = sz.search_params(k=10, cut=5, heap_factor=0.9, wave=4, persistent=True, order=order, learned=learned,
+                             max_query_nnz=dq.max_row_nnz)
+        i, s = sz.seismic_search(ix, dq, p)
+        torch.cuda.synchronize()
+        out.append((i.cpu(), s.cpu()))
+    for i, s in out[1:]:
+        assert torch.equal(i, out[0][0]) and torch.equal(s, out[0][1])
