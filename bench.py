@@ -684,12 +684,13 @@ def main():
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample",
                                                    "single_thread_us_per_query", "single_thread_sample")}
     del ox
-    if not args.no_compact and w.get("compact"):
+    extras = world == 1  # the scaling runs report the timed throughput only
+    if extras and not args.no_compact and w.get("compact"):
         line["compact"] = compact_eval(args, w, sz, docs, dq, gt_sc, knn_graph, best, launch, stream,
                                        lambda index, p_, n: time_runs(p_, n, index=index))
-    if not args.no_learned and w.get("n_train"):
+    if extras and not args.no_learned and w.get("n_train"):
         line["learned"] = learned_eval(args, w, sz, ix, dq, gt_sc, stream, time_runs, launch)
-    if not args.no_serve and w.get("serve_rates"):
+    if extras and not args.no_serve and w.get("serve_rates"):
         line["serving"] = serving_eval(args, w, sz, ix, best, bool(line.get("learned")), launch)
     line["bench_seconds"] = time.time() - t_all
     if rank == 0:
