@@ -65,7 +65,8 @@ METRIC = "QPS at recall@10>=0.9 (batched Seismic search, fixed parameters)"
 # kernel on the 300k-document workload (fp32 rows, wave 8), keyed by the L2 row prefetch (which
 # brings whole rows in); used to estimate a full launch's traffic from its executed bytes.  A form
 # without a capture of the current kernel reports null.
-TRAFFIC_PER_EXEC_BYTE = {False: None, True: None}
+TRAFFIC_PER_EXEC_BYTE = {False: (14.940076544e9 + 0.615757056e9) / 24.652337535e9,
+                         True: (19.571495424e9 + 0.855928576e9) / 24.652337535e9}
 
 
 def log(*a):
