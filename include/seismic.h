@@ -244,6 +244,16 @@ enum {
   SEISMIC_X_SUM_VAL,        /* float[n_summary_entries]: max-summary values */
   SEISMIC_X_SUM_CODE,       /* uint8[n_summary_entries]: 8-bit codes */
   SEISMIC_X_CENT,           /* uint32[n_postings]: per list position, assigned cluster index */
+  /* the term-major summaries the search reads (always kept) */
+  SEISMIC_X_SBM,            /* uint32[dim * W * 2], W = ceil(dim / 32): per list t and 32-term word w,
+                               the presence bits of t's summary terms, then the index of the word's
+                               first column */
+  SEISMIC_X_SCPTR,          /* uint32[columns + dim]: column pointers into SCOL_*; each list's
+                               pointers end with a sentinel */
+  SEISMIC_X_SCOL_BLK,       /* uint16[n_summary_entries]: block (index within its list), ascending
+                               within a column */
+  SEISMIC_X_SCOL_CODE,      /* uint8[n_summary_entries]: 8-bit codes (quantised indexes) */
+  SEISMIC_X_SCOL_VAL,       /* float[n_summary_entries]: values (fp32 summaries) */
   SEISMIC_X_N
 };
 int seismic_export(const seismic_index *index, int32_t what, void *dst, uint64_t cap_bytes,

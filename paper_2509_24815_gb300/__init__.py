@@ -28,10 +28,11 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUDGET, EIO = 0, -1, -2, -3, -4, -5, -6
 STATS = ("lists", "blocks_scored", "blocks_evaluated", "blocks_skipped", "docs", "doc_nnz", "knn_docs",
          "summary_entries", "knn_nnz", "dir_lookups", "block_docs", "query_nnz", "t_start_ns", "t_end_ns")
 EXPORTS = ("list_ptr", "list_doc", "blk_ptr", "bdoc_ptr", "bdoc", "blk_m", "blk_size", "sum_ptr", "sum_term",
-           "sum_val", "sum_code", "cent")
+           "sum_val", "sum_code", "cent", "sbm", "scptr", "scol_blk", "scol_code", "scol_val")
 _EXPORT_DT = dict(list_ptr=np.uint32, list_doc=np.uint32, blk_ptr=np.uint32, bdoc_ptr=np.uint32, bdoc=np.uint32,
                   blk_m=np.float32, blk_size=np.float32, sum_ptr=np.uint32, sum_term=np.uint16,
-                  sum_val=np.float32, sum_code=np.uint8, cent=np.uint32)
+                  sum_val=np.float32, sum_code=np.uint8, cent=np.uint32, sbm=np.uint32, scptr=np.uint32,
+                  scol_blk=np.uint16, scol_code=np.uint8, scol_val=np.float32)
 MLP_IN, MLP_PARAMS = 64, 128 * 64 + 128 + 64 * 128 + 64 + 2 * 64 + 2
 
 

@@ -2,11 +2,12 @@
 //
 // Host (threads): validation, forward-index layout, posting lists pruned to
 // their top-lambda values (Set alpha-MSS, fixed-lambda form of Table 4, or the
-// proportional form of Definition "Set alpha-MSS"), centroid sampling,
-// blocks, max summaries (Eq. "summary") with their alpha-MSS and 8-bit
-// quantisation (Section 4.1.3), and the term-major summary layout.
-// Device: the shallow k-means assignment (Section 4.1.2), which dominates the
-// build: every list member against every centroid of its list.
+// proportional form of Definition "Set alpha-MSS"), centroid sampling and
+// blocks.
+// Device: the shallow k-means assignment (Section 4.1.2): every list member
+// against every centroid of its list; then (summary.cu) the max summaries
+// (Eq. "summary") with their alpha-MSS and 8-bit quantisation (Section
+// 4.1.3), and the term-major summary layout the search reads.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -379,21 +380,23 @@ int build_index(const seismic_csr *docs, const seismic_build_params *bp, seismic
       if (units > 0xFFFFFFFFull) return fail(SEISMIC_EINVAL, "forward index exceeds 2^32 32-byte units");
     }
     std::vector<uint8_t> data((size_t)units * kUnitBytes, 0);
-    parallel_for((int64_t)D.n, T, [&](int64_t i, int) {
-      const uint64_t n = D.ip[i + 1] - D.ip[i];
-      const uint32_t nch = (uint32_t)(frow[i] >> 32);
-      uint8_t *rec = data.data() + (size_t)(uint32_t)frow[i] * kUnitBytes;
-      for (uint64_t p = 0; p < n; p++) {
-        const uint64_t o = p / kChunk, e = p % kChunk;
-        const uint16_t t = D.t[D.ip[i] + p];
-        const float v = D.v[D.ip[i] + p];
-        if (fp16) {
-          std::memcpy(rec + o * kUnitBytes + 2 * e, &t, 2);
-          const __half hv = __float2half_rn(v);  // exact: v is already an fp16 value
-          std::memcpy(rec + o * kUnitBytes + 16 + 2 * e, &hv, 2);
-        } else {
-          std::memcpy(rec + 2 * p, &t, 2);
-          std::memcpy(rec + (size_t)kUnitBytes * ((nch + 1) / 2) + 4 * p, &v, 4);
+    parallel_ranges((int64_t)D.n, T, 4096, [&](int64_t i0, int64_t i1) {
+      for (int64_t i = i0; i < i1; i++) {
+        const uint64_t n = D.ip[i + 1] - D.ip[i];
+        const uint32_t nch = (uint32_t)(frow[i] >> 32);
+        uint8_t *rec = data.data() + (size_t)(uint32_t)frow[i] * kUnitBytes;
+        for (uint64_t p = 0; p < n; p++) {
+          const uint64_t o = p / kChunk, e = p % kChunk;
+          const uint16_t t = D.t[D.ip[i] + p];
+          const float v = D.v[D.ip[i] + p];
+          if (fp16) {
+            std::memcpy(rec + o * kUnitBytes + 2 * e, &t, 2);
+            const __half hv = __float2half_rn(v);  // exact: v is already an fp16 value
+            std::memcpy(rec + o * kUnitBytes + 16 + 2 * e, &hv, 2);
+          } else {
+            std::memcpy(rec + 2 * p, &t, 2);
+            std::memcpy(rec + (size_t)kUnitBytes * ((nch + 1) / 2) + 4 * p, &v, 4);
+          }
         }
       }
     });
@@ -518,11 +521,12 @@ int build_index(const seismic_csr *docs, const seismic_build_params *bp, seismic
   timer.mark("centroids");
   // ---- clustering on the device
   std::vector<uint32_t> assign(npost);
+  DevBuf d_ip, d_t, d_v;  // the collection on the device: clustering, then the summaries
   {
     std::vector<uint32_t> work;
     for (uint32_t t = 0; t < d; t++)
       if (lptr[t + 1] > lptr[t]) work.push_back(t);
-    DevBuf d_work, d_lptr, d_ldoc, d_cptr, d_cdoc, d_ip, d_t, d_v, d_best, d_asg;
+    DevBuf d_work, d_lptr, d_ldoc, d_cptr, d_cdoc, d_best, d_asg;
     if ((rc = upload(d_work, work)) || (rc = upload(d_lptr, lptr)) || (rc = upload(d_ldoc, ldoc)) ||
         (rc = upload(d_cptr, cptr2)) || (rc = upload(d_cdoc, cdoc)) || (rc = upload(d_ip, D.ip)) ||
         (rc = upload(d_t, D.t)) || (rc = upload(d_v, D.v)) || (rc = d_best.alloc(npost * 8)) ||
@@ -591,221 +595,130 @@ int build_index(const seismic_csr *docs, const seismic_build_params *bp, seismic
   std::vector<uint32_t>().swap(cdoc);
 
   timer.mark("blocks");
-  // ---- summaries: max vector, alpha-MSS, quantisation (per list, block-major)
-  struct ListSum {
-    std::vector<uint32_t> cnt;  // kept entries per block
-    std::vector<uint16_t> term;
-    std::vector<float> val;
-    std::vector<uint8_t> code;
-    std::vector<float> m, size;
-  };
-  std::vector<ListSum> ls(d);
-  const double alpha = bp->alpha;
+  // ---- summaries (max vector, alpha-MSS, u8) and their term-major layout, on the device
   const int quant = bp->quantize_u8 ? 1 : 0;
-  {
-    std::vector<std::vector<float>> mx(T, std::vector<float>(d));
-    std::vector<std::vector<uint32_t>> cn(T, std::vector<uint32_t>(d, 0));
-    std::vector<std::vector<uint16_t>> touched(T, std::vector<uint16_t>(d));
-    std::vector<std::vector<uint64_t>> ms(T, std::vector<uint64_t>(d));
-    parallel_for(d, T, [&](int64_t t, int tid) {
-      ListSum &L = ls[t];
-      uint32_t g0 = bptr[t], g1 = bptr[t + 1];
-      L.cnt.resize(g1 - g0);
-      L.m.resize(g1 - g0);
-      L.size.resize(g1 - g0);
-      float *mxx = mx[tid].data();
-      uint32_t *cc = cn[tid].data();
-      uint16_t *tch = touched[tid].data();
-      uint64_t *buf = ms[tid].data();
-      for (uint32_t g = g0; g < g1; g++) {
-        uint32_t bs = bdptr[g + 1] - bdptr[g], nt = 0;
-        for (uint32_t m = bdptr[g]; m < bdptr[g + 1]; m++) {
-          uint32_t j = bdoc[m];
-          for (uint64_t p = D.ip[j]; p < D.ip[j + 1]; p++) {
-            uint16_t s = D.t[p];
-            float v = D.v[p];
-            if (cc[s] == 0) {
-              tch[nt++] = s;
-              mxx[s] = v;
-            } else if (v > mxx[s]) {
-              mxx[s] = v;
-            }
-            cc[s]++;
-          }
-        }
-        // the summary's nonzero coordinates as keys that sort by (|phi| desc, term asc):
-        // the bits of |phi| (a non-negative float orders like its bits) complemented,
-        // then the term; phi itself stays in mxx[term] for the rest of this block
-        uint32_t ne = 0;
-        for (uint32_t i = 0; i < nt; i++) {
-          uint16_t s = tch[i];
-          float phi = mxx[s];
-          if (cc[s] < bs && phi < 0.0f) mxx[s] = phi = 0.0f;  // members without the term contribute 0
-          cc[s] = 0;
-          if (phi != 0.0f) {
-            uint32_t ab;
-            const float a = std::fabs(phi);
-            std::memcpy(&ab, &a, 4);
-            buf[ne++] = ((uint64_t)(0xFFFFFFFFu - ab) << 16) | s;
-          }
-        }
-        std::sort(buf, buf + ne);
-        auto mass = [](uint64_t key) {
-          const uint32_t ab = 0xFFFFFFFFu - (uint32_t)(key >> 16);
-          float a;
-          std::memcpy(&a, &ab, 4);
-          return (double)a;
-        };
-        double total = 0.0;
-        for (uint32_t i = 0; i < ne; i++) total += mass(buf[i]);
-        double target = alpha * total, c = 0.0;
-        uint32_t keep = ne;
-        for (uint32_t i = 0; i < ne; i++) {
-          c += mass(buf[i]);
-          if (c >= target) {
-            keep = i + 1;
-            break;
-          }
-        }
-        for (uint32_t i = 0; i < keep; i++) buf[i] &= 0xFFFFull;  // the kept terms, to sort ascending
-        std::sort(buf, buf + keep);
-        float lo = INFINITY, hi = -INFINITY;
-        size_t base = L.term.size();
-        for (uint32_t i = 0; i < keep; i++) {
-          const uint16_t tt = (uint16_t)buf[i];
-          const float v = mxx[tt];
-          L.term.push_back(tt);
-          L.val.push_back(v);
-          lo = std::min(lo, v);
-          hi = std::max(hi, v);
-        }
-        if (keep == 0) lo = hi = 0.0f;
-        float size = (float)(((double)hi - (double)lo) / 256.0);
-        L.m[g - g0] = lo;
-        L.size[g - g0] = size;
-        L.cnt[g - g0] = keep;
-        if (quant)
-          for (uint32_t i = 0; i < keep; i++) {
-            double q = size > 0.0f ? std::floor(((double)L.val[base + i] - (double)lo) / (double)size) : 0.0;
-            q = std::min(255.0, std::max(0.0, q));
-            L.code.push_back((uint8_t)q);
-          }
-      }
-    });
-  }
-  timer.mark("summaries (max, alpha-MSS, u8)");
-  std::vector<uint32_t> sptr(nblk + 1, 0);
-  {
-    uint64_t acc = 0;
-    for (uint32_t t = 0; t < d; t++)
-      for (uint32_t b = 0; b < ls[t].cnt.size(); b++) {
-        sptr[bptr[t] + b] = (uint32_t)acc;
-        acc += ls[t].cnt[b];
-        if (acc > 0xFFFFFFFFull) return fail(SEISMIC_EINVAL, "more than 2^32 summary entries");
-      }
-    sptr[nblk] = (uint32_t)acc;
-    ix->n_sum = acc;
-  }
-  const uint64_t nsum = ix->n_sum;
-  {  // bound on |summary value| as the search reconstructs it (m + code * size)
-    double mx = 0.0;
-    for (uint32_t t = 0; t < d; t++) {
-      const ListSum &L = ls[t];
-      if (quant) {
-        for (size_t b = 0; b < L.m.size(); b++)
-          mx = std::max(mx, std::fabs((double)L.m[b]) + 256.0 * (double)L.size[b]);
-      } else {
-        for (float v : L.val) mx = std::max(mx, (double)std::fabs(v));
-      }
-    }
-    ix->sum_absmax = (float)(mx * 1.001 + 1e-30);
-  }
-  {
-    // the block-major copies are kept only for export
-    const bool keep_bm = bp->keep_block_summaries != 0;
-    std::vector<uint16_t> sterm(keep_bm ? nsum : 0);
-    std::vector<float> sval(keep_bm ? nsum : 0), bm(nblk), bsz(nblk);
-    std::vector<uint8_t> scode(keep_bm && quant ? nsum : 0);
-    std::vector<uint16_t> cblk(nsum);
-    std::vector<uint8_t> ccode(quant ? nsum : 0);
-    std::vector<float> cval(quant ? 0 : nsum);
-    // directory: presence bitmap of each list's summary terms, column base per
-    // 32-term word, and per-list column pointers (columns + 1 sentinel)
-    const uint32_t W = (d + 31) / 32;
-    std::vector<uint32_t> ncols(d, 0);
-    parallel_for(d, T, [&](int64_t t, int) {
-      std::vector<uint8_t> has(d, 0);
-      for (uint16_t s : ls[t].term) has[s] = 1;
-      uint32_t c = 0;
-      for (uint32_t s = 0; s < d; s++) c += has[s];
-      ncols[t] = c;
-    });
-    std::vector<uint64_t> cbase(d + 1, 0);
-    for (uint32_t t = 0; t < d; t++) cbase[t + 1] = cbase[t] + ncols[t] + 1;
-    if (cbase[d] > 0xFFFFFFFFull) return fail(SEISMIC_EINVAL, "more than 2^32 summary columns");
-    std::vector<uint32_t> sbmv((size_t)d * W * 2, 0u), cptrv(cbase[d]);
-    parallel_for(d, T, [&](int64_t t, int) {
-      const ListSum &L = ls[t];
-      uint32_t g0 = bptr[t], nb = bptr[t + 1] - g0;
-      uint32_t base = sptr[g0];
-      for (uint32_t b = 0; b < nb; b++) {
-        bm[g0 + b] = L.m[b];
-        bsz[g0 + b] = L.size[b];
-      }
-      if (keep_bm && !L.term.empty()) {
-        std::memcpy(&sterm[base], L.term.data(), L.term.size() * 2);
-        std::memcpy(&sval[base], L.val.data(), L.val.size() * 4);
-        if (quant) std::memcpy(&scode[base], L.code.data(), L.code.size());
-      }
-      // term-major layout of this list: columns by term, blocks ascending inside a column
-      std::vector<uint32_t> cnt(d, 0), cur(d, 0);
-      for (uint16_t s : L.term) cnt[s]++;
-      uint32_t run = base, col = (uint32_t)cbase[t];
-      uint32_t *bw = sbmv.data() + (size_t)t * W * 2;
-      for (uint32_t s = 0; s < d; s++) {
-        if ((s & 31) == 0) bw[2 * (s >> 5) + 1] = col;
-        if (!cnt[s]) continue;
-        bw[2 * (s >> 5)] |= 1u << (s & 31);
-        cptrv[col++] = run;
-        cur[s] = run;
-        run += cnt[s];
-      }
-      cptrv[col] = run;  // the list's sentinel
-      uint32_t e = 0;
-      for (uint32_t b = 0; b < nb; b++)
-        for (uint32_t i = 0; i < L.cnt[b]; i++, e++) {
-          uint32_t o = cur[L.term[e]]++;
-          cblk[o] = (uint16_t)b;
-          if (quant) ccode[o] = L.code[e];
-          else cval[o] = L.val[e];
-        }
-    });
-    if (ix->max_blocks_per_list > 65535) return fail(SEISMIC_EINVAL, "more than 65535 blocks in a list");
-    std::vector<ListSum>().swap(ls);
-    if ((rc = upload(ix->blk_m, bm)) || (rc = upload(ix->blk_size, bsz)) || (rc = upload(ix->scol_blk, cblk)))
-      return rc;
-    if (bp->keep_block_summaries) {
-      if ((rc = upload(ix->sum_ptr, sptr)) || (rc = upload(ix->sum_term, sterm)) || (rc = upload(ix->sum_val, sval)))
-        return rc;
-      if (quant && (rc = upload(ix->sum_code, scode))) return rc;
-    }
-    if (quant) {
-      if ((rc = upload(ix->scol_code, ccode))) return rc;
-    } else if ((rc = upload(ix->scol_val, cval))) {
-      return rc;
-    }
-    if ((rc = upload(ix->sbm, sbmv)) || (rc = upload(ix->scptr, cptrv))) return rc;
-  }
+  const bool keep_bm = bp->keep_block_summaries != 0;  // the block-major copies are kept only for export
+  const uint32_t W = (d + 31) / 32;
+  if (ix->max_blocks_per_list > 65535) return fail(SEISMIC_EINVAL, "more than 65535 blocks in a list");
   if ((rc = upload(ix->list_ptr, lptr)) || (rc = upload(ix->list_doc, ldoc)) || (rc = upload(ix->cent, assign)) ||
       (rc = upload(ix->blk_ptr, bptr)) || (rc = upload(ix->bdoc_ptr, bdptr)) || (rc = upload(ix->bdoc, bdoc)))
     return rc;
+  {
+    int sms = 1, occ = 1;
+    SZ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ix->device));
+    if ((rc = sum_occupancy(W, &occ))) return rc;
+    const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(nblk, (uint64_t)sms * occ));
+    uint32_t gstride = 1;
+    while (gstride < d) gstride <<= 1;
+    DevBuf d_keep, d_thr, d_babs, d_gphi, d_gkeys;
+    if ((rc = ix->blk_m.alloc((size_t)nblk * 4)) || (rc = ix->blk_size.alloc((size_t)nblk * 4)) ||
+        (rc = d_keep.alloc((size_t)nblk * 4)) || (rc = d_thr.alloc((size_t)nblk * 8)) ||
+        (rc = d_babs.alloc((size_t)nblk * 8)) || (rc = d_gphi.alloc((size_t)grid * gstride * 4)) ||
+        (rc = d_gkeys.alloc((size_t)grid * gstride * 8)))
+      return rc;
+    SumArgs sa{};
+    sa.ip = d_ip.as<uint64_t>();
+    sa.t = d_t.as<uint16_t>();
+    sa.v = d_v.as<float>();
+    sa.bdptr = ix->bdoc_ptr.as<uint32_t>();
+    sa.bdoc = ix->bdoc.as<uint32_t>();
+    sa.nblk = nblk;
+    sa.W = W;
+    sa.alpha = bp->alpha;
+    sa.quant = quant;
+    sa.keep = d_keep.as<uint32_t>();
+    sa.thr = d_thr.as<unsigned long long>();
+    sa.bm = ix->blk_m.as<float>();
+    sa.bsz = ix->blk_size.as<float>();
+    sa.babs = d_babs.as<double>();
+    sa.gphi = d_gphi.as<uint32_t>();
+    sa.gkeys = d_gkeys.as<unsigned long long>();
+    sa.gstride = gstride;
+    if ((rc = launch_sum_pass(sa, 1, grid, 0))) return rc;
+    SZ_CUDA(cudaDeviceSynchronize());
+    std::vector<uint32_t> keep(nblk), sptr(nblk + 1, 0);
+    std::vector<double> babs(nblk);
+    if (nblk) {
+      SZ_CUDA(cudaMemcpy(keep.data(), d_keep.p, (size_t)nblk * 4, cudaMemcpyDeviceToHost));
+      SZ_CUDA(cudaMemcpy(babs.data(), d_babs.p, (size_t)nblk * 8, cudaMemcpyDeviceToHost));
+    }
+    uint64_t acc = 0;
+    double mx = 0.0;  // bound on |summary value| as the search reconstructs it (m + code * size)
+    for (uint64_t g = 0; g < nblk; g++) {
+      sptr[g] = (uint32_t)acc;
+      acc += keep[g];
+      if (acc > 0xFFFFFFFFull) return fail(SEISMIC_EINVAL, "more than 2^32 summary entries");
+      mx = std::max(mx, babs[g]);
+    }
+    sptr[nblk] = (uint32_t)acc;
+    ix->n_sum = acc;
+    ix->sum_absmax = (float)(mx * 1.001 + 1e-30);
+    const uint64_t nsum = acc;
+    timer.mark("summaries: max, alpha-MSS, u8 (device)");
+    if ((rc = upload(ix->sum_ptr, sptr)) || (rc = ix->sum_term.alloc(nsum * 2)) ||
+        ((!quant || keep_bm) && (rc = ix->sum_val.alloc(nsum * 4))) || (quant && (rc = ix->sum_code.alloc(nsum))))
+      return rc;
+    sa.sptr = ix->sum_ptr.as<uint32_t>();
+    sa.sterm = ix->sum_term.as<uint16_t>();
+    sa.sval = ix->sum_val.p ? ix->sum_val.as<float>() : nullptr;
+    sa.scode = ix->sum_code.as<uint8_t>();
+    if ((rc = launch_sum_pass(sa, 2, grid, 0))) return rc;
+    // the term-major columns of each list, behind the presence-bitmap directory
+    DevBuf d_ncols, d_cbase, d_cur;
+    if ((rc = ix->sbm.alloc((size_t)d * W * 8)) || (rc = d_ncols.alloc((size_t)d * 4))) return rc;
+    ColArgs ca{};
+    ca.dim = d;
+    ca.W = W;
+    ca.blk_ptr = ix->blk_ptr.as<uint32_t>();
+    ca.sptr = ix->sum_ptr.as<uint32_t>();
+    ca.sterm = ix->sum_term.as<uint16_t>();
+    ca.sval = sa.sval;
+    ca.scode = sa.scode;
+    ca.quant = quant;
+    ca.sbm = ix->sbm.as<uint2>();
+    ca.ncols = d_ncols.as<uint32_t>();
+    const uint32_t cgrid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(d, (uint64_t)sms * 8));
+    if ((rc = launch_cols_pass(ca, 1, cgrid, 0))) return rc;
+    std::vector<uint32_t> ncols(d), cbase(d);
+    SZ_CUDA(cudaMemcpy(ncols.data(), d_ncols.p, (size_t)d * 4, cudaMemcpyDeviceToHost));
+    uint64_t cacc = 0;
+    for (uint32_t t = 0; t < d; t++) {
+      cbase[t] = (uint32_t)cacc;
+      cacc += ncols[t] + 1ull;  // the list's columns and its sentinel
+      if (cacc > 0xFFFFFFFFull) return fail(SEISMIC_EINVAL, "more than 2^32 summary columns");
+    }
+    if ((rc = upload(d_cbase, cbase)) || (rc = ix->scptr.alloc(cacc * 4)) || (rc = d_cur.alloc(cacc * 4)) ||
+        (rc = ix->scol_blk.alloc(nsum * 2)) || (quant && (rc = ix->scol_code.alloc(nsum))) ||
+        (!quant && (rc = ix->scol_val.alloc(nsum * 4))))
+      return rc;
+    ca.cbase = d_cbase.as<uint32_t>();
+    ca.scptr = ix->scptr.as<uint32_t>();
+    ca.cur = d_cur.as<uint32_t>();
+    ca.cblk = ix->scol_blk.as<uint16_t>();
+    ca.ccode = ix->scol_code.as<uint8_t>();
+    ca.cval = ix->scol_val.as<float>();
+    if ((rc = launch_cols_pass(ca, 2, cgrid, 0))) return rc;
+    SZ_CUDA(cudaDeviceSynchronize());
+    if (!keep_bm) {
+      ix->sum_ptr.release();
+      ix->sum_term.release();
+      ix->sum_val.release();
+      ix->sum_code.release();
+    }
+  }
+  d_ip.release();
+  d_t.release();
+  d_v.release();
+  timer.mark("summary layout (device)");
   {  // each member's forward row (first unit, chunk count) beside its id: one dependent load fewer
     std::vector<uint64_t> brow(npost);
-    parallel_for((int64_t)npost, T, [&](int64_t p, int) { brow[p] = frow[bdoc[p]]; });
+    parallel_ranges((int64_t)npost, T, 1 << 16, [&](int64_t p0, int64_t p1) {
+      for (int64_t p = p0; p < p1; p++) brow[p] = frow[bdoc[p]];
+    });
     if ((rc = upload(ix->bdoc_row, brow))) return rc;
   }
   SZ_CUDA(cudaDeviceSynchronize());
-  timer.mark("summary layout, uploads");
+  timer.mark("member rows");
   *out = ix.release();
   return SEISMIC_OK;
 }

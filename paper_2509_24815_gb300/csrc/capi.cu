@@ -705,6 +705,11 @@ int export_impl(const seismic_index *ix, int32_t what, void *dst, uint64_t cap, 
     case SEISMIC_X_SUM_VAL: b = &ix->sum_val; n = ix->n_sum * 4; break;
     case SEISMIC_X_SUM_CODE: b = &ix->sum_code; n = ix->bp.quantize_u8 ? ix->n_sum : 0; break;
     case SEISMIC_X_CENT: b = &ix->cent; n = ix->n_postings * 4; break;
+    case SEISMIC_X_SBM: b = &ix->sbm; n = b->p ? b->bytes : 0; break;
+    case SEISMIC_X_SCPTR: b = &ix->scptr; n = b->p ? b->bytes : 0; break;
+    case SEISMIC_X_SCOL_BLK: b = &ix->scol_blk; n = b->p ? b->bytes : 0; break;
+    case SEISMIC_X_SCOL_CODE: b = &ix->scol_code; n = b->p ? b->bytes : 0; break;
+    case SEISMIC_X_SCOL_VAL: b = &ix->scol_val; n = b->p ? b->bytes : 0; break;
     default: return fail(SEISMIC_EINVAL, "unknown export id");
   }
   if (n && !b->p) return fail(SEISMIC_EINVAL, "array not kept: build with keep_block_summaries = 1");

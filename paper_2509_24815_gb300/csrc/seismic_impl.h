@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstdint>
 #include <cstring>
@@ -63,6 +64,14 @@ inline void parallel_for(int64_t n, int threads, const std::function<void(int64_
       }
     });
   for (auto &x : th) x.join();
+}
+
+// Runs fn(lo, hi) over [0, n) in ranges of `grain` items, on `threads`
+// workers: for loops whose items are too small to be handed out one by one.
+inline void parallel_ranges(int64_t n, int threads, int64_t grain,
+                            const std::function<void(int64_t, int64_t)> &fn) {
+  const int64_t parts = (n + grain - 1) / grain;
+  parallel_for(parts, threads, [&](int64_t r, int) { fn(r * grain, std::min(n, (r + 1) * grain)); });
 }
 
 // ---------------------------------------------------------------- device memory
@@ -200,6 +209,53 @@ struct seismic_index {
 };
 
 namespace seismic {
+// Block summaries on the device (summary.cu).
+struct SumArgs {
+  const uint64_t *ip;  // the collection: CSR rows (terms ascending, no zeros)
+  const uint16_t *t;
+  const float *v;
+  const uint32_t *bdptr;  // u32[nblk + 1]: members of block g
+  const uint32_t *bdoc;
+  uint64_t nblk;
+  uint32_t W;  // ceil(dim / 32)
+  double alpha;
+  int quant;
+  // pass 1 outputs: kept entries, key of the last kept one, (m, size), bound on |value|
+  uint32_t *keep;
+  unsigned long long *thr;
+  float *bm, *bsz;
+  double *babs;
+  // pass 2 outputs, block-major at sptr[g] (sval may be NULL)
+  const uint32_t *sptr;
+  uint16_t *sterm;
+  float *sval;
+  uint8_t *scode;
+  // scratch for blocks with more distinct terms than shared memory holds:
+  // gstride phi words and keys per CTA of the launch
+  uint32_t *gphi;
+  unsigned long long *gkeys;
+  uint32_t gstride;
+};
+struct ColArgs {
+  uint32_t dim, W;
+  const uint32_t *blk_ptr, *sptr;
+  const uint16_t *sterm;
+  const float *sval;
+  const uint8_t *scode;
+  int quant;
+  uint2 *sbm;             // uint2[dim * W]: presence bits, first column index of the word
+  uint32_t *ncols;        // u32[dim]: columns of list t (count pass)
+  const uint32_t *cbase;  // u32[dim]: first column of list t (fill pass)
+  uint32_t *scptr, *cur;  // column pointers (+ one sentinel per list), cursors
+  uint16_t *cblk;
+  uint8_t *ccode;
+  float *cval;
+};
+// grid: CTAs of the launch (the scratch holds gstride entries for each)
+int launch_sum_pass(const SumArgs &a, int pass, uint32_t grid, cudaStream_t st);
+int launch_cols_pass(const ColArgs &a, int pass, uint32_t grid, cudaStream_t st);
+int sum_occupancy(uint32_t W, int *blocks);
+
 uint64_t device_bytes(const seismic_index *ix);
 int validate_host_csr(const seismic_csr *m, const char *what, uint32_t dim_expect);
 }  // namespace seismic

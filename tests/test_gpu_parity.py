@@ -52,6 +52,48 @@ def compare_index(sz, ix, ox, dim, quant):
             np.testing.assert_array_equal(ex["sum_code"][sp[g0]:sp[g1]], L["scode"], err_msg=f"codes {t}")
 
 
+def term_major_from_block_major(ex, dim, quant):
+    """The search's term-major summary layout, restated from the block-major
+    export: per list, a column per summary term (ascending), holding the
+    list's blocks with that term in ascending order; a presence bitmap and the
+    first column index per 32-term word; column pointers ending with a
+    sentinel per list."""
+    bp, sp, st = ex["blk_ptr"], ex["sum_ptr"], ex["sum_term"]
+    sv = ex["sum_code"] if quant else ex["sum_val"]
+    W = (dim + 31) // 32
+    sbm = np.zeros((dim, W, 2), dtype=np.uint32)
+    scptr, blk, val = [], np.empty(len(st), dtype=np.uint16), np.empty(len(st), dtype=sv.dtype)
+    col = 0
+    for t in range(dim):
+        g0, g1 = int(bp[t]), int(bp[t + 1])
+        e0, e1 = int(sp[g0]), int(sp[g1])
+        terms = st[e0:e1].astype(np.int64)
+        b = np.repeat(np.arange(g1 - g0), np.diff(sp[g0:g1 + 1]).astype(np.int64))
+        order = np.lexsort((b, terms))
+        blk[e0:e1] = b[order]
+        val[e0:e1] = sv[e0:e1][order]
+        uniq, cnt = np.unique(terms, return_counts=True)
+        scptr.extend((e0 + np.concatenate(([0], np.cumsum(cnt)))).tolist())
+        has = np.zeros(W * 32, dtype=bool)
+        has[uniq] = True
+        words = has.reshape(W, 32)
+        sbm[t, :, 0] = (words * (1 << np.arange(32, dtype=np.uint64))).sum(axis=1).astype(np.uint32)
+        sbm[t, :, 1] = col + np.concatenate(([0], np.cumsum(words.sum(axis=1))[:-1]))
+        col += len(uniq) + 1
+    return sbm.reshape(-1), np.array(scptr, dtype=np.uint32), blk, val
+
+
+def check_term_major(sz, ix, dim, quant):
+    ex = {w: sz.seismic_export(ix, w) for w in ("blk_ptr", "sum_ptr", "sum_term", "sum_val", "sum_code", "sbm",
+                                                "scptr", "scol_blk", "scol_code", "scol_val")
+          if not (w == "sum_code" and not quant)}
+    sbm, scptr, blk, val = term_major_from_block_major(ex, dim, quant)
+    np.testing.assert_array_equal(ex["sbm"], sbm, err_msg="directory")
+    np.testing.assert_array_equal(ex["scptr"], scptr, err_msg="column pointers")
+    np.testing.assert_array_equal(ex["scol_blk"], blk, err_msg="column blocks")
+    np.testing.assert_array_equal(ex["scol_code"] if quant else ex["scol_val"], val, err_msg="column values")
+
+
 def check_exact_ids(docs, queries, gids, gsc, oids, osc, tol=TOL):
     """ids equal up to near-ties; scores within tol of the fp64 values."""
     gids = np.asarray(gids).astype(np.uint32)
@@ -83,6 +125,36 @@ def test_index_equals_oracle_small(sz, small, small_built, quant):
 
 def test_index_equals_oracle_c1(sz, c1):
     compare_index(sz, c1["ix"], c1["ox"], c1["docs"].dim, False)
+
+
+@pytest.mark.parametrize("quant", [True, False])
+def test_term_major_layout_small(sz, small, small_built, quant):
+    check_term_major(sz, small_built[quant][0], small["docs"].dim, quant)
+
+
+def test_term_major_layout_c1(sz, c1):
+    check_term_major(sz, c1["ix"], c1["docs"].dim, False)
+
+
+@pytest.mark.parametrize("quant", [True, False])
+def test_blocks_beyond_shared_memory(sz, quant):
+    """One block per list and unpruned lists: the blocks of frequent terms hold
+    thousands of documents and more distinct terms than the summary kernels
+    keep in shared memory (4096), so their max vectors, sketches and sorts run
+    in the global scratch; the index must still equal the oracle's."""
+    docs = synth.docs(6000, seed=3, K=8)
+    lam, beta = 100_000, 1
+    ix = sz.seismic_build(docs, lambda_=lam, beta=beta, alpha=0.4, quantize_u8=quant, seed=2,
+                          keep_block_summaries=True)
+    ox = oracle.Index(docs, lam, beta, 0.4, quant, seed=2)
+    # the largest block's distinct terms (the union of its members' rows)
+    bd, bdp = sz.seismic_export(ix, "bdoc"), sz.seismic_export(ix, "bdoc_ptr")
+    g = int(np.argmax(np.diff(bdp)))
+    rows = [docs.row(int(j))[0] for j in bd[bdp[g]:bdp[g + 1]]]
+    assert len(np.unique(np.concatenate(rows))) > 4096
+    compare_index(sz, ix, ox, docs.dim, quant)
+    check_term_major(sz, ix, docs.dim, quant)
+    ix.close()
 
 
 # ------------------------------------------------------------------ exhaustive
