@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libseismic.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["build.cu", "summary.cu", "search.cu", "search_warp.cu", "exact.cu", "capi.cu", "mlp.cu", "noalloc.cu", "serve.cu"]
+SOURCES = ["build.cu", "prune.cu", "summary.cu", "search.cu", "search_warp.cu", "exact.cu", "capi.cu", "mlp.cu", "noalloc.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
          "-I" + INCLUDE]

@@ -1,13 +1,13 @@
 // Index construction: Algorithm "Indexing with Seismic" (Section 4.4).
 //
-// Host (threads): validation, forward-index layout, posting lists pruned to
-// their top-lambda values (Set alpha-MSS, fixed-lambda form of Table 4, or the
-// proportional form of Definition "Set alpha-MSS"), centroid sampling and
-// blocks.
-// Device: the shallow k-means assignment (Section 4.1.2): every list member
-// against every centroid of its list; then (summary.cu) the max summaries
-// (Eq. "summary") with their alpha-MSS and 8-bit quantisation (Section
-// 4.1.3), and the term-major summary layout the search reads.
+// Host (threads): validation, forward-index layout, full posting lists,
+// centroid sampling and blocks.
+// Device: the posting lists pruned to their top-lambda values (prune.cu; Set
+// alpha-MSS, fixed-lambda form of Table 4, or the proportional form of
+// Definition "Set alpha-MSS"); the shallow k-means assignment (Section 4.1.2):
+// every list member against every centroid of its list; then (summary.cu) the
+// max summaries (Eq. "summary") with their alpha-MSS and 8-bit quantisation
+// (Section 4.1.3), and the term-major summary layout the search reads.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -129,9 +129,10 @@ uint64_t splitmix64_next(uint64_t &state) {
 // sequential merge of the two sorted rows.  Argmax ties keep the lower
 // centroid index.
 constexpr int kAsgThreads = 128;
-constexpr int kAsgCC = 64;        // centroids per chunk (cluster index fits in u8)
+constexpr int kAsgCC = 48;        // centroids per chunk (cluster index fits in u8); 2 CTAs per SM
 constexpr int kAsgMaxEnt = 8192;  // nonzeros per chunk (= kMaxRowNnzBuild bound below)
 static_assert(kMaxRowNnzBuild <= kAsgMaxEnt, "a centroid row must fit one chunk");
+static_assert((size_t)kAsgCC * kAsgThreads * 8 >= (size_t)(kAsgMaxEnt + 1) * 4, "the cursors share the accumulators");
 
 __device__ __forceinline__ void asg_scan_rank(const uint32_t *bits, uint16_t *rank, uint32_t W, uint32_t *wtmp) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kAsgThreads / 32;
@@ -204,9 +205,11 @@ __global__ void __launch_bounds__(kAsgThreads) k_assign(
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t W = (dim + 31) / 32;
   double *acc = reinterpret_cast<double *>(smem);                    // kAsgCC * kAsgThreads
+  // the chunk's per-term counts and cursors (kAsgMaxEnt + 1) live in the
+  // accumulators' space: they are dead once the chunk's index is built
+  uint32_t *ccur = reinterpret_cast<uint32_t *>(smem);
   float *ent_w = reinterpret_cast<float *>(acc + kAsgCC * kAsgThreads);  // kAsgMaxEnt
-  uint32_t *ccur = reinterpret_cast<uint32_t *>(ent_w + kAsgMaxEnt);     // kAsgMaxEnt + 1
-  uint32_t *cbits = ccur + (kAsgMaxEnt + 1);                              // W
+  uint32_t *cbits = reinterpret_cast<uint32_t *>(ent_w + kAsgMaxEnt);    // W
   uint16_t *coff = reinterpret_cast<uint16_t *>(cbits + W);               // kAsgMaxEnt + 1
   uint16_t *crank = coff + (kAsgMaxEnt + 1);                              // W
   uint8_t *ent_c = reinterpret_cast<uint8_t *>(crank + W);                // kAsgMaxEnt
@@ -309,8 +312,8 @@ __global__ void __launch_bounds__(kAsgThreads) k_assign(
 
 size_t asg_smem_bytes(uint32_t dim) {
   uint32_t W = (dim + 31) / 32;
-  return (size_t)kAsgCC * kAsgThreads * 8 + (size_t)kAsgMaxEnt * 4 + (size_t)(kAsgMaxEnt + 1) * 4 + W * 4 +
-         (size_t)(kAsgMaxEnt + 1) * 2 + W * 2 + kAsgMaxEnt + 16;
+  return (size_t)kAsgCC * kAsgThreads * 8 + (size_t)kAsgMaxEnt * 4 + W * 4 + (size_t)(kAsgMaxEnt + 1) * 2 + W * 2 +
+         kAsgMaxEnt + 16;
 }
 
 }  // namespace
@@ -469,25 +472,39 @@ int build_index(const seismic_csr *docs, const seismic_build_params *bp, seismic
   const uint64_t npost = lptr[d];
   ix->n_postings = npost;
   std::vector<uint32_t> ldoc(npost);
-  std::vector<float> lval(npost);
-  parallel_for(d, T, [&](int64_t t, int) {
-    uint64_t a = fptr[t], n = fptr[t + 1] - a;
-    if (!n) return;
-    std::vector<uint32_t> idx(n);
-    for (uint64_t i = 0; i < n; i++) idx[i] = (uint32_t)i;
-    uint64_t lam = lptr[t + 1] - lptr[t];
-    auto cmp = [&](uint32_t x, uint32_t y) {
-      float vx = fval[a + x], vy = fval[a + y];
-      if (vx != vy) return vx > vy;
-      return fdoc[a + x] < fdoc[a + y];
-    };
-    if (lam < n) std::partial_sort(idx.begin(), idx.begin() + lam, idx.end(), cmp);
-    else std::sort(idx.begin(), idx.end(), cmp);
-    for (uint64_t i = 0; i < lam; i++) {
-      ldoc[lptr[t] + i] = fdoc[a + idx[i]];
-      lval[lptr[t] + i] = fval[a + idx[i]];
+  {
+    // on the device: each list's top-lambda_t by (value desc, doc asc), from the full lists
+    DevBuf d_fptr, d_fdoc, d_fval, d_lptr, d_ldoc;
+    const uint32_t *gdoc = ix->full_doc.as<uint32_t>();
+    const float *gval = ix->full_val.as<float>();
+    if ((rc = upload(d_fptr, fptr)) || (rc = upload(d_lptr, lptr)) || (rc = d_ldoc.alloc(npost * 4))) return rc;
+    if (!ix->has_full) {
+      if ((rc = upload(d_fdoc, fdoc)) || (rc = upload(d_fval, fval))) return rc;
+      gdoc = d_fdoc.as<uint32_t>();
+      gval = d_fval.as<float>();
     }
-  });
+    uint32_t cap = 0;
+    if ((rc = launch_prune(d_fptr.as<uint64_t>(), gdoc, gval, d_lptr.as<uint32_t>(), d, d_ldoc.as<uint32_t>(), &cap,
+                           0)))
+      return rc;
+    SZ_CUDA(cudaDeviceSynchronize());
+    if (npost) SZ_CUDA(cudaMemcpy(ldoc.data(), d_ldoc.p, npost * 4, cudaMemcpyDeviceToHost));
+    // lists whose lambda_t exceeds what the device sorts in shared memory: on host threads
+    parallel_for(d, T, [&](int64_t t, int) {
+      const uint64_t a = fptr[t], n = fptr[t + 1] - a, lam = lptr[t + 1] - lptr[t];
+      if (lam <= cap) return;
+      std::vector<uint32_t> idx(n);
+      for (uint64_t i = 0; i < n; i++) idx[i] = (uint32_t)i;
+      auto cmp = [&](uint32_t x, uint32_t y) {
+        float vx = fval[a + x], vy = fval[a + y];
+        if (vx != vy) return vx > vy;
+        return fdoc[a + x] < fdoc[a + y];
+      };
+      if (lam < n) std::partial_sort(idx.begin(), idx.begin() + lam, idx.end(), cmp);
+      else std::sort(idx.begin(), idx.end(), cmp);
+      for (uint64_t i = 0; i < lam; i++) ldoc[lptr[t] + i] = fdoc[a + idx[i]];
+    });
+  }
   std::vector<uint64_t>().swap(fptr);
   std::vector<uint32_t>().swap(fdoc);
   std::vector<float>().swap(fval);

@@ -251,6 +251,11 @@ struct ColArgs {
   uint8_t *ccode;
   float *cval;
 };
+// Pruned lists (prune.cu): ldoc[lptr[t] ..] = list t's top (lptr[t+1] - lptr[t])
+// postings by (value desc, doc asc), for every list whose count is at most *cap
+// (set by the call); the others are left for the host.
+int launch_prune(const uint64_t *fptr, const uint32_t *fdoc, const float *fval, const uint32_t *lptr, uint32_t dim,
+                 uint32_t *ldoc, uint32_t *cap, cudaStream_t st);
 // grid: CTAs of the launch (the scratch holds gstride entries for each)
 int launch_sum_pass(const SumArgs &a, int pass, uint32_t grid, cudaStream_t st);
 int launch_cols_pass(const ColArgs &a, int pass, uint32_t grid, cudaStream_t st);

@@ -136,6 +136,23 @@ def test_term_major_layout_c1(sz, c1):
     check_term_major(sz, c1["ix"], c1["docs"].dim, False)
 
 
+@pytest.mark.parametrize("lam", [3000, 9000])
+def test_pruning_long_lists(sz, lam):
+    """Lists longer than the device prunes by one shared-memory sort (8192
+    postings): with lambda = 3000 they are cut by the radix select, with
+    lambda = 9000 (above that cap) the longest are pruned on host threads.
+    Values rounded to fp16 tie often, so the (value desc, doc asc) order is
+    exercised on ties."""
+    docs = synth.docs(40_000, seed=4, K=4)
+    d16 = synth.CSR(docs.indptr, docs.terms, docs.vals.astype(np.float16).astype(np.float32), docs.dim)
+    df = np.bincount(docs.terms, minlength=docs.dim)
+    assert (df > 9000).sum() > 10
+    ix = sz.seismic_build(d16, lambda_=lam, beta=8, alpha=0.4, quantize_u8=True, seed=1, keep_block_summaries=True)
+    ox = oracle.Index(d16, lam, 8, 0.4, True, seed=1)
+    compare_index(sz, ix, ox, docs.dim, True)
+    ix.close()
+
+
 @pytest.mark.parametrize("quant", [True, False])
 def test_blocks_beyond_shared_memory(sz, quant):
     """One block per list and unpruned lists: the blocks of frequent terms hold
