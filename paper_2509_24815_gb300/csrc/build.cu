@@ -201,6 +201,7 @@ __global__ void __launch_bounds__(kAsgThreads) k_assign(
     const uint32_t *__restrict__ list_doc, const uint32_t *__restrict__ cent_ptr,
     const uint32_t *__restrict__ cent_doc, const uint64_t *__restrict__ indptr,
     const uint16_t *__restrict__ terms, const float *__restrict__ vals, uint32_t dim,
+    const unsigned long long *__restrict__ fwd_row, const uint8_t *__restrict__ fwd, int fp16,
     double *__restrict__ best, uint32_t *__restrict__ assign) {
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t W = (dim + 31) / 32;
@@ -272,16 +273,32 @@ __global__ void __launch_bounds__(kAsgThreads) k_assign(
       for (uint32_t i = tid; i < n; i += kAsgThreads) {
         const uint32_t j = list_doc[lp0 + i];
         for (uint32_t cc = 0; cc < ncc; cc++) a[cc * kAsgThreads] = 0.0;
-        for (uint64_t p = indptr[j]; p < indptr[j + 1]; p++) {
-          const uint16_t s = terms[p];
-          const uint32_t w = cbits[s >> 5];
-          const uint32_t bit = 1u << (s & 31);
-          if (!(w & bit)) continue;
-          const uint32_t idx = crank[s >> 5] + __popc(w & (bit - 1u));
-          const double u = (double)vals[p];
-          for (uint32_t e = coff[idx]; e < coff[idx + 1]; e++)
-            a[(uint32_t)ent_c[e] * kAsgThreads] = __dadd_rn(a[(uint32_t)ent_c[e] * kAsgThreads],
-                                                              __dmul_rn(u, (double)ent_w[e]));
+        // the member's terms in ascending order, 8 per 16-byte load from its
+        // forward-index record; a value is read only where the chunk holds the term
+        const unsigned long long row = fwd_row[j];
+        const uint8_t *rec = fwd + (size_t)(uint32_t)row * kUnitBytes;
+        const uint32_t nch = (uint32_t)(row >> 32), nnz = (uint32_t)(indptr[j + 1] - indptr[j]);
+        for (uint32_t o = 0; o < nch; o++) {
+          const uint4 tq = *reinterpret_cast<const uint4 *>(rec + (size_t)o * (fp16 ? kUnitBytes : 16u));
+          const uint32_t tw[4] = {tq.x, tq.y, tq.z, tq.w};
+#pragma unroll
+          for (uint32_t e8 = 0; e8 < kChunk; e8++) {
+            if (o * kChunk + e8 >= nnz) break;  // the padding after the row's last entry
+            const uint32_t s = (e8 & 1) ? (tw[e8 >> 1] >> 16) : (tw[e8 >> 1] & 0xFFFFu);
+            const uint32_t w = cbits[s >> 5];
+            const uint32_t bit = 1u << (s & 31);
+            if (!(w & bit)) continue;
+            const uint32_t idx = crank[s >> 5] + __popc(w & (bit - 1u));
+            double u;
+            if (fp16) {
+              u = (double)__half2float(*reinterpret_cast<const __half *>(rec + (size_t)o * kUnitBytes + 16 + 2 * e8));
+            } else {
+              u = (double)*reinterpret_cast<const float *>(rec + (size_t)kUnitBytes * ((nch + 1) / 2 + o) + 4 * e8);
+            }
+            for (uint32_t e = coff[idx]; e < coff[idx + 1]; e++)
+              a[(uint32_t)ent_c[e] * kAsgThreads] = __dadd_rn(a[(uint32_t)ent_c[e] * kAsgThreads],
+                                                                __dmul_rn(u, (double)ent_w[e]));
+          }
         }
         double bv;
         uint32_t bc, cc0;
@@ -558,6 +575,7 @@ int build_index(const seismic_csr *docs, const seismic_build_params *bp, seismic
       k_assign<<<grid, kAsgThreads, smem>>>(d_work.as<uint32_t>(), (uint32_t)work.size(), d_lptr.as<uint32_t>(),
                                             d_ldoc.as<uint32_t>(), d_cptr.as<uint32_t>(), d_cdoc.as<uint32_t>(),
                                             d_ip.as<uint64_t>(), d_t.as<uint16_t>(), d_v.as<float>(), d,
+                                            ix->fwd_row.as<unsigned long long>(), ix->fwd_data.as<uint8_t>(), fp16,
                                             d_best.as<double>(), d_asg.as<uint32_t>());
       SZ_CUDA(cudaGetLastError());
       SZ_CUDA(cudaDeviceSynchronize());
