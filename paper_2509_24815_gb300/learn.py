@@ -95,6 +95,28 @@ def lagrangian_labels(table, target: float, margin: float = 0.01):
     return cuts[g], hfs[g], r, float(by[np.arange(len(g)), g].mean())
 
 
+def standardize(features: np.ndarray):
+    """Per-feature mean and spread of the training features (spread 1 where a
+    feature is constant); the features differ in scale by two orders of
+    magnitude (values near 1, their L1 norm up to ~200)."""
+    f = np.asarray(features, dtype=np.float64)
+    mu, sd = f.mean(axis=0), f.std(axis=0)
+    sd[sd < 1e-6] = 1.0
+    return mu, sd
+
+
+def fold_input_scaling(weights: np.ndarray, mu: np.ndarray, sd: np.ndarray) -> np.ndarray:
+    """Weights trained on (x - mu) / sd, rewritten to take x itself:
+    W1 <- W1 / sd (per input column), b1 <- b1 - (W1 / sd) mu.  The installed
+    network and the inference kernels then see raw features."""
+    w = np.array(weights, dtype=np.float64, copy=True)
+    n1 = 128 * 64
+    w1 = w[:n1].reshape(128, 64) / sd[None, :]
+    w[:n1] = w1.ravel()
+    w[n1:n1 + 128] = w[n1:n1 + 128] - w1 @ mu
+    return w.astype(np.float32)
+
+
 def targets_from_labels(cut, hf) -> np.ndarray:
     t0 = (np.asarray(cut, dtype=np.float64) - CUT_LO) / CUT_SPAN
     t1 = (np.asarray(hf, dtype=np.float64) - HF_LO) / HF_SPAN
@@ -195,16 +217,28 @@ def calibrate(index, weights: np.ndarray, queries: DeviceCSR, gt_scores, k: int,
 
 def fit(index, train_queries: DeviceCSR, host_train_queries, k: int = 10, target: float = 0.9,
         quantized: bool = True, steps: int = 3000, lr: float = 2e-3, seed: int = 0, base_params=None,
-        val_frac: float = 0.2, grid_cut=GRID_CUT, grid_hf=GRID_HF, max_shift: float = 12.0):
+        val_frac: float = 0.2, grid_cut=GRID_CUT, grid_hf=GRID_HF, max_shift: float = 12.0,
+        standardize_features: bool = False, table=None):
     """Labels (trade-off form), features, training on the first part of the
-    training queries, calibration on the rest; installs the network."""
-    cut0, hf0, table = label_queries(index, train_queries, k, target, quantized, grid_cut=grid_cut, grid_hf=grid_hf,
-                                     base_params=base_params)
+    training queries, calibration on the rest; installs the network.  With
+    `standardize_features` the network trains on standardized features and
+    their mean and spread are folded into its first layer afterwards.
+    `table`, the grid runs of an earlier call on the same queries, skips the
+    labelling runs."""
+    if table is None:
+        _, _, table = label_queries(index, train_queries, k, target, quantized, grid_cut=grid_cut, grid_hf=grid_hf,
+                                    base_params=base_params)
     cut, hf, lab_rec, lab_bytes = lagrangian_labels(table, target)
     feats = seismic_query_features(index, host_train_queries)
     n = host_train_queries.n_rows
     ntr = max(1, int(n * (1.0 - val_frac)))
-    w, trace = train(feats[:ntr], targets_from_labels(cut[:ntr], hf[:ntr]), steps=steps, lr=lr, seed=seed)
+    tgt = targets_from_labels(cut[:ntr], hf[:ntr])
+    if standardize_features:
+        mu, sd = standardize(feats[:ntr])
+        w, trace = train(((feats[:ntr] - mu) / sd).astype(np.float32), tgt, steps=steps, lr=lr, seed=seed)
+        w = fold_input_scaling(w, mu, sd)
+    else:
+        w, trace = train(feats[:ntr], tgt, steps=steps, lr=lr, seed=seed)
     val_host = host_train_queries.slice(ntr, n)
     val = DeviceCSR.from_host(val_host)
     _, gt_val = seismic_search_exact(index, val, k)
