@@ -29,6 +29,9 @@ MUTATIONS = [
     ("lists keep the smallest values",
      "  if (a->v > b->v) return -1;\n  if (a->v < b->v) return 1;\n  return (a->doc > b->doc) - (a->doc < b->doc);",
      "  if (a->v < b->v) return -1;\n  if (a->v > b->v) return 1;\n  return (a->doc > b->doc) - (a->doc < b->doc);"),
+    ("list ties at the cut go to the higher document id (reading R2)",
+     "  if (a->v < b->v) return 1;\n  return (a->doc > b->doc) - (a->doc < b->doc);",
+     "  if (a->v < b->v) return 1;\n  return (a->doc < b->doc) - (a->doc > b->doc);"),
     ("blocks visited in ascending score", "  if (a->r > b->r) return -1;\n  if (a->r < b->r) return 1;",
      "  if (a->r < b->r) return -1;\n  if (a->r > b->r) return 1;"),
     ("exact top-k without the query weight", "acc[dd] += qv * (double)c->L->val[e];",

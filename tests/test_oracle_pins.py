@@ -236,6 +236,29 @@ def test_build_invariants(small, alpha, quant):
                     assert (code == 0).all()
 
 
+def test_pruning_tie_break_across_the_cut():
+    """Values rounded to one decimal tie often, so in many lists the lambda-th
+    posting sits inside a run of equal values: each list is still the
+    top-lambda by (value desc, doc asc) (reading R2), ties at the cut going to
+    the lower document ids."""
+    docs = synth.docs(1500, seed=6, d=300, K=8)
+    vals = np.maximum(np.round(docs.vals, 1), 0.1).astype(np.float32)
+    tied = synth.CSR(docs.indptr, docs.terms, vals, docs.dim)
+    lam = 70
+    X = oracle.Index(tied, lam, 9, 0.4, True, seed=3, threads=4)
+    Dd = tied.to_dense()
+    straddle = 0
+    for t in range(tied.dim):
+        col = Dd[:, t]
+        full = np.nonzero(col)[0]
+        ref = full[np.lexsort((full, -col[full]))][:lam]
+        np.testing.assert_array_equal(X.list(t)["doc"], ref, err_msg=f"list {t}")
+        if len(full) > lam:
+            left_out = np.setdiff1d(full, ref)
+            straddle += int(col[left_out].max() == col[ref[-1]])
+    assert straddle > 20, straddle
+
+
 def test_summary_conservative_at_alpha_one(small):
     """Eq. summary: with alpha = 1 and no quantisation, <q, phi(B)> >= <q, u_j>
     for every member j and any non-negative q."""
